@@ -1,0 +1,249 @@
+"""FP64 CPU oracle of the generic LISA response (arXiv:2204.06633) -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference arm of
+``bench.py`` may import this package.  The CUDA library never does, and the oracle shares
+no code with it.  The arithmetic lives in ``lr_oracle.c`` (plain C, FP64, each function
+citing the paper's section or equation it follows); this module only compiles it with gcc
+and marshals numpy arrays.
+
+Array layouts (all float64, C-contiguous):
+  positions  pos[3 spacecraft][3 xyz][n_knots]   (m)
+  delays     del[6 links][n_knots]               (s), link order 12, 23, 31, 13, 32, 21
+  links      y[6][N]                             on the output grid t0 + n dt
+  TDI        xyz[3][N]                           X, Y, Z
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lr_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liblr_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NOT_A_KNOT = 0
+NATURAL = 1
+DELAY_SUM = 0
+DELAY_NESTED = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile lr_oracle.c into oracle/_build/liblr_oracle.so (gcc, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        D, I64, I, P = ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
+        dp = ctypes.POINTER(ctypes.c_double)
+        lp = ctypes.POINTER(ctypes.c_int64)
+        sig = {
+            "orc_set_threads": (I, [I]),
+            "orc_lagrange_weights": (None, [I, D, dp]),
+            "orc_lagrange_dweights": (None, [I, D, dp]),
+            "orc_lagrange_read": (D, [dp, I64, I64, D, I]),
+            "orc_spline_eval_series": (I, [dp, I64, dp, I, dp, I64, dp]),
+            "orc_orbit_new": (P, [dp, I64, dp, dp, I, ctypes.POINTER(ctypes.c_int)]),
+            "orc_orbit_free": (None, [P]),
+            "orc_orbit_eval": (None, [P, D, dp, dp]),
+            "orc_orbit_delays_at_knots": (None, [P, dp]),
+            "orc_sky_basis": (None, [D, D, dp, dp, dp]),
+            "orc_project": (I, [I, D, D, I64, P, dp, dp, I64, D, D, D, D, dp]),
+            "orc_project_abs": (I, [I, D, D, I64, P, dp, dp, I64, D, D, D, D, dp]),
+            "orc_project_at": (I, [I, D, D, I64, P, dp, dp, I64, D, D, D, D, lp, I64, dp]),
+            "orc_tdi": (I, [I, I, I, D, D, I64, P, dp, dp]),
+            "orc_tdi_abs": (I, [I, I, I, D, D, I64, P, dp, dp]),
+            "orc_response_at": (I, [I, I, I, D, D, I64, P, P, dp, dp, I64, D, D, D, D, lp, I64, dp, I]),
+            "orc_tdi_adjoint": (I, [I, I, I, D, D, I64, P, dp, dp]),
+            "orc_project_adjoint": (I, [I, D, D, I64, P, I64, D, D, D, D, dp, dp, dp]),
+            "orc_sky_gradient": (I, [I, D, D, I64, P, dp, dp, I64, D, D, D, D, dp, dp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise RuntimeError(f"oracle {what} failed with status {status}")
+
+
+def set_threads(n: int) -> int:
+    """Set the OpenMP thread count of the oracle; returns the count in effect."""
+    return int(_load().orc_set_threads(int(n)))
+
+
+# ---------------------------------------------------------------- Lagrange
+def lagrange_weights(p: int, eps: float) -> np.ndarray:
+    w = np.empty(p + 1)
+    _load().orc_lagrange_weights(p, float(eps), _dp(w))
+    return w
+
+
+def lagrange_dweights(p: int, eps: float) -> np.ndarray:
+    w = np.empty(p + 1)
+    _load().orc_lagrange_dweights(p, float(eps), _dp(w))
+    return w
+
+
+def lagrange_read(s, base: int, u: float, p: int) -> float:
+    s = _f64(s)
+    return float(_load().orc_lagrange_read(_dp(s), len(s), int(base), float(u), p))
+
+
+# ---------------------------------------------------------------- splines and orbits
+def spline_eval(t_knots, y, t, bc: int = NOT_A_KNOT) -> np.ndarray:
+    tk, yy, tt = _f64(t_knots), _f64(y), _f64(np.atleast_1d(t))
+    out = np.empty(len(tt))
+    _check(_load().orc_spline_eval_series(_dp(tk), len(tk), _dp(yy), bc, _dp(tt), len(tt), _dp(out)), "spline")
+    return out
+
+
+class Orbit:
+    """Spline-interpolated spacecraft positions and link delays (delays=None: solve the
+    Newtonian light-time equation on the knots)."""
+
+    def __init__(self, t_knots, pos, delays=None, bc: int = NOT_A_KNOT):
+        lib = _load()
+        self.t_knots = _f64(t_knots)
+        self._pos = _f64(pos).reshape(9, -1)
+        self._del = None if delays is None else _f64(delays).reshape(6, -1)
+        st = ctypes.c_int(0)
+        self._h = lib.orc_orbit_new(_dp(self.t_knots), len(self.t_knots), _dp(self._pos),
+                                    None if self._del is None else _dp(self._del), bc, ctypes.byref(st))
+        if not self._h:
+            raise RuntimeError(f"oracle orbit construction failed with status {st.value}")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.orc_orbit_free(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def eval(self, t: float):
+        """(positions [3][3], delays [6]) at time t."""
+        p9, d6 = np.empty(9), np.empty(6)
+        _load().orc_orbit_eval(self._h, float(t), _dp(p9), _dp(d6))
+        return p9.reshape(3, 3), d6
+
+    def delays_at_knots(self) -> np.ndarray:
+        out = np.empty((6, len(self.t_knots)))
+        _load().orc_orbit_delays_at_knots(self._h, _dp(out))
+        return out
+
+
+def sky_basis(lam: float, beta: float):
+    k, u, v = np.empty(3), np.empty(3), np.empty(3)
+    _load().orc_sky_basis(float(lam), float(beta), _dp(k), _dp(u), _dp(v))
+    return k, u, v
+
+
+# ---------------------------------------------------------------- response
+def project(p, dt, t0, n, porb: Orbit, hp, hc, t0h, lam, beta, psi, absval: bool = False) -> np.ndarray:
+    hp, hc = _f64(hp), _f64(hc)
+    y = np.empty((6, n))
+    fn = _load().orc_project_abs if absval else _load().orc_project
+    _check(fn(p, dt, t0, n, porb.handle, _dp(hp), _dp(hc), len(hp), t0h, lam, beta, psi, _dp(y)), "project")
+    return y
+
+
+def project_at(p, dt, t0, n, porb: Orbit, hp, hc, t0h, lam, beta, psi, idx) -> np.ndarray:
+    hp, hc = _f64(hp), _f64(hc)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    y = np.empty((6, len(idx)))
+    _check(_load().orc_project_at(p, dt, t0, n, porb.handle, _dp(hp), _dp(hc), len(hp), t0h, lam, beta, psi,
+                                  idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(idx), _dp(y)),
+           "project_at")
+    return y
+
+
+def tdi(p, gen, dt, t0, n, torb: Orbit, y, delay_mode: int = DELAY_SUM, absval: bool = False) -> np.ndarray:
+    y = _f64(y)
+    xyz = np.empty((3, n))
+    fn = _load().orc_tdi_abs if absval else _load().orc_tdi
+    _check(fn(p, gen, delay_mode, dt, t0, n, torb.handle, _dp(y), _dp(xyz)), "tdi")
+    return xyz
+
+
+def response(p, gen, dt, t0, n, porb, torb, hp, hc, t0h, lam, beta, psi, delay_mode: int = DELAY_SUM,
+             absval: bool = False) -> np.ndarray:
+    """Projection followed by TDI over the whole output span."""
+    y = project(p, dt, t0, n, porb, hp, hc, t0h, lam, beta, psi, absval=absval)
+    return tdi(p, gen, dt, t0, n, torb, y, delay_mode, absval=absval)
+
+
+def response_at(p, gen, dt, t0, n, porb, torb, hp, hc, t0h, lam, beta, psi, idx,
+                delay_mode: int = DELAY_SUM, absval: bool = False) -> np.ndarray:
+    """X, Y, Z at selected output indices (y computed on demand around each)."""
+    hp, hc = _f64(hp), _f64(hc)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    xyz = np.empty((3, len(idx)))
+    _check(_load().orc_response_at(p, gen, delay_mode, dt, t0, n, porb.handle, torb.handle, _dp(hp), _dp(hc),
+                                   len(hp), t0h, lam, beta, psi,
+                                   idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(idx), _dp(xyz),
+                                   1 if absval else 0), "response_at")
+    return xyz
+
+
+# ---------------------------------------------------------------- adjoints
+def tdi_adjoint(p, gen, dt, t0, n, torb: Orbit, gxyz, delay_mode: int = DELAY_SUM) -> np.ndarray:
+    g = _f64(gxyz)
+    gy = np.empty((6, n))
+    _check(_load().orc_tdi_adjoint(p, gen, delay_mode, dt, t0, n, torb.handle, _dp(g), _dp(gy)), "tdi_adjoint")
+    return gy
+
+
+def project_adjoint(p, dt, t0, n, porb: Orbit, nh, t0h, lam, beta, psi, gy):
+    gy = _f64(gy)
+    ghp, ghc = np.empty(nh), np.empty(nh)
+    _check(_load().orc_project_adjoint(p, dt, t0, n, porb.handle, nh, t0h, lam, beta, psi, _dp(gy), _dp(ghp),
+                                       _dp(ghc)), "project_adjoint")
+    return ghp, ghc
+
+
+def sky_gradient(p, dt, t0, n, porb: Orbit, hp, hc, t0h, lam, beta, psi, gy) -> np.ndarray:
+    hp, hc, gy = _f64(hp), _f64(hc), _f64(gy)
+    g = np.empty(3)
+    _check(_load().orc_sky_gradient(p, dt, t0, n, porb.handle, _dp(hp), _dp(hc), len(hp), t0h, lam, beta, psi,
+                                    _dp(gy), _dp(g)), "sky_gradient")
+    return g
+
+
+def backward(p, gen, dt, t0, n, porb, torb, hp, hc, t0h, lam, beta, psi, gxyz, delay_mode: int = DELAY_SUM):
+    """Gradient of <gxyz, R(h)> with respect to h+, hx and (lambda, beta, psi)."""
+    gy = tdi_adjoint(p, gen, dt, t0, n, torb, gxyz, delay_mode)
+    ghp, ghc = project_adjoint(p, dt, t0, n, porb, len(hp), t0h, lam, beta, psi, gy)
+    gsky = sky_gradient(p, dt, t0, n, porb, hp, hc, t0h, lam, beta, psi, gy)
+    return ghp, ghc, gsky
