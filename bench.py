@@ -1,0 +1,342 @@
+#!/usr/bin/env python
+"""Benchmark of the generic LISA response (projection onto six links + second-generation TDI).
+
+Workload (the batched configuration the headline metric is quoted on): 1024 Galactic binaries
+(f log-uniform 0.1-10 mHz, isotropic sky, A = 1e-22, fdot = 1e-17), each with its own length
+N_s uniform in [2^16, 2^20] samples at dt = 10 s, flexing Keplerian orbit splined from a 1e5 s
+knot grid, Lagrange order 25, one persistent launch per step.  A step = one batched
+projection+TDI-2 pass over the whole batch; the metric is link-samples/s = 6 * sum N_s / time.
+
+Output: one JSON line (rank 0).  `value` is device-resident throughput (inputs already in HBM);
+`e2e` the same through the C ABI with host buffers (pinned H2D of h+, hx and D2H of X, Y, Z
+inside the timed region).  `--impl reference` times the FP64 CPU oracle instead (a bounded
+sample of the same workload, on the host's cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "link-samples/s for projection+TDI-2 (batched mixed vs FP64) at stated rel. error"
+DT, T0, ORDER, S_SOURCES = 10.0, 0.0, 25, 1024
+# algorithmic work per output sample at order p (T = p + 1 taps): tap multiply-adds 60 T
+# (9 unique projection reads x 2 polarisations + 42 TDI reads) = 120 T flops, 51 Lagrange
+# weight vectors x ~3 T flops, ~500 flops of orbit splines and geometry
+FLOPS_PER_SAMPLE = lambda p: 273 * (p + 1) + 500  # noqa: E731
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (nominal; our DFMA probe measured 1.20)
+
+
+def workload(rank: int, n_sources: int):
+    seed = 3 + 1000 * rank
+    lens = synth.ragged_lengths(n_sources, seed=seed)
+    srcs = synth.draw_sources(n_sources, seed=seed + 1, A=1e-22, fdot=1e-17)
+    return lens, srcs
+
+
+def build_inputs(lens, srcs, p):
+    """Packed h+, hx with each source's input margins, CSR offsets, t0_h and sky."""
+    m = synth.input_margin_samples(DT, p)
+    nh = lens + 2 * m
+    h_off = np.concatenate([[0], np.cumsum(nh)]).astype(np.int64)
+    out_off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    hp = np.empty(h_off[-1])
+    hc = np.empty(h_off[-1])
+    t0h = np.full(len(lens), T0 - m * DT)
+    for s, src in enumerate(srcs):
+        t = synth.sample_grid(t0h[s], DT, int(nh[s]))
+        a, b = synth.gb_polarisations(src, t)
+        hp[h_off[s]:h_off[s + 1]] = a
+        hc[h_off[s]:h_off[s + 1]] = b
+    sky = np.array([[s.lam, s.beta, s.psi] for s in srcs])
+    return h_off, out_off, t0h, sky, hp, hc
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_rate(lens, srcs, p, orb, budget_s=12.0, sources=4):
+    """The FP64 oracle (as it stands) on a bounded sample of the workload: the first `sources`
+    sources, each truncated to a prefix sized so the whole sample takes about budget_s."""
+    import oracle
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    o = oracle.Orbit(orb.t_knots, orb.pos, None)
+    # calibrate on a short prefix
+    n_try = 2000
+    src = srcs[0]
+    t0h, hp, hc = synth.gb_input(src, T0, DT, n_try, p)
+    t = time.perf_counter()
+    oracle.response(p, 2, DT, T0, n_try, o, o, hp, hc, t0h, src.lam, src.beta, src.psi)
+    per_sample = (time.perf_counter() - t) / n_try
+    n_each = int(max(1000, min(int(min(lens[:sources])), budget_s / per_sample / sources)))
+    total, elapsed = 0, 0.0
+    for src in srcs[:sources]:
+        t0h, hp, hc = synth.gb_input(src, T0, DT, n_each, p)
+        t = time.perf_counter()
+        oracle.response(p, 2, DT, T0, n_each, o, o, hp, hc, t0h, src.lam, src.beta, src.psi)
+        elapsed += time.perf_counter() - t
+        total += n_each
+    return {"value": 6 * total / elapsed, "unit": "link-samples/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {sources} sources of the batch, first {n_each} output samples each "
+                      f"({total} samples, {elapsed:.1f} s, FP64 C oracle, OpenMP over samples)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    lens, srcs = workload(0, S_SOURCES)
+    orb = synth.orbit_flexing(T0 - 3e5, T0 + DT * int(lens.max()) + 3e5)
+    times = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        cb = oracle_rate(lens, srcs, ORDER, orb, budget_s=max(2.0, 40.0 / (args.warmup + args.steps)))
+        if i >= args.warmup:
+            times.append(cb["value"])
+    v = statistics.median(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "link-samples/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batched 1024 Galactic binaries, N_s ~ U[2^16, 2^20], dt 10 s, flexing "
+                                   "Keplerian orbit, order 25, TDI-2", "sample": cb["sample"]},
+            "cpu_baseline": {"value": v, "unit": "link-samples/s", "cores": cb["cores"], "kind": "oracle",
+                             "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": "link-samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2204_06633_gb300 as lr
+
+    p = args.order
+    lens, srcs = workload(rank, args.sources)
+    total_samples = int(lens.sum())
+    orb = synth.orbit_flexing(T0 - 3e5, T0 + DT * int(lens.max()) + 3e5)
+    h_off, out_off, t0h, sky, hp, hc = build_inputs(lens, srcs, p)
+
+    ctx = lr.Context(local)
+    o = lr.Orbit(ctx, orb.t_knots, orb.pos, None)
+    precision = lr.MIXED if args.precision == "mixed" else lr.FP64
+    plan = lr.Plan(ctx, p, 1, DT, o, t0=T0, precision=precision, tile=args.tile)
+    d_hoff = torch.tensor(h_off, device=dev)
+    d_ooff = torch.tensor(out_off, device=dev)
+    d_t0h = torch.tensor(t0h, device=dev)
+    d_sky = torch.tensor(sky, device=dev)
+    d_hp = torch.tensor(hp, device=dev)
+    d_hc = torch.tensor(hc, device=dev)
+    d_xyz = torch.empty(3 * total_samples, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.response_batched(d_hoff, d_ooff, d_t0h, d_sky, d_hp, d_hc, d_xyz, stream=stream)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    plan.check(stream)
+    barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    plan.check(stream)
+    ms_total = t_start.elapsed_time(t_end)
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(ms, op=dist.ReduceOp.MAX)
+    ms_step = float(ms.item()) / args.steps
+    link_samples = 6.0 * total_samples * ws
+    value = link_samples / (ms_step * 1e-3)
+
+    # accuracy at the stated precision: sampled outputs of a few sources against the oracle
+    rel_err = None
+    if rank == 0 and not args.no_check:
+        rel_err = sampled_error(d_xyz, lens, srcs, out_off, orb, p)
+
+    # end to end: pinned host buffers, H2D of the strain and D2H of X, Y, Z inside the region
+    e2e = None
+    if not args.no_e2e:
+        hp_pin = torch.from_numpy(hp).pin_memory()
+        hc_pin = torch.from_numpy(hc).pin_memory()
+        out_pin = torch.empty(3 * total_samples, dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            d_hp.copy_(hp_pin, non_blocking=True)
+            d_hc.copy_(hc_pin, non_blocking=True)
+            step()
+            out_pin.copy_(d_xyz, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n_e2e = max(1, min(args.steps, 3))
+        a.record(stream)
+        for _ in range(n_e2e):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        t = torch.tensor([a.elapsed_time(b) / n_e2e], dtype=torch.float64, device=dev)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e = {"value": link_samples / (float(t.item()) * 1e-3), "unit": "link-samples/s",
+               "h2d_bytes_per_step": int(hp.nbytes + hc.nbytes), "d2h_bytes_per_step": int(out_pin.numel() * 8)}
+
+    if rank != 0:
+        return
+    avg_launch_s = statistics.mean(launch_ms) * 1e-3
+    flops = FLOPS_PER_SAMPLE(p) * total_samples
+    peak_tflops = FP64_NOMINAL_TFLOPS
+    roof = {"bound": "alu", "achieved": flops / avg_launch_s / 1e12, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": flops / avg_launch_s / 1e12 / peak_tflops, "traffic": None,
+            "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (own DFMA probe: 1.20)",
+            "algorithmic_flops_per_sample": FLOPS_PER_SAMPLE(p)}
+    line = {"metric": METRIC, "value": value, "unit": "link-samples/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if precision == lr.FP64 else "f32 taps + f64 index",
+            "data": "synthetic",
+            "config": {"workload": "batched 1024 Galactic binaries, N_s ~ U[2^16, 2^20] (sum %d), dt 10 s, "
+                                   "flexing Keplerian orbit (1e5 s knots), order %d, TDI-2, fused projection+TDI, "
+                                   "one persistent launch per step" % (total_samples, p),
+                       "precision": args.precision, "sources_per_gpu": args.sources,
+                       "samples_per_gpu": total_samples, "l2": "inputs (%.1f GB) larger than L2" %
+                       ((hp.nbytes + hc.nbytes) / 1e9), "tile": plan.desc.tile},
+            "rel_error_vs_oracle": rel_err, "roofline": roof, "e2e": e2e, "gpu_launches": 2 * args.steps,
+            "clocks": clk.summary()}
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = oracle_rate(lens, srcs, p, orb)
+    print(json.dumps(line), flush=True)
+
+
+def sampled_error(d_xyz, lens, srcs, out_off, orb, p, n_sources=6, n_idx=60):
+    """Max over a few sources of the relative L2 error of sampled X, Y, Z against the oracle."""
+    import oracle
+    o = oracle.Orbit(orb.t_knots, orb.pos, None)
+    rng = np.random.default_rng(7)
+    worst = 0.0
+    for s in rng.choice(len(lens), n_sources, replace=False):
+        N = int(lens[s])
+        idx = np.sort(rng.integers(0, N, n_idx))
+        src = srcs[s]
+        t0h, hp, hc = synth.gb_input(src, T0, DT, N, p)
+        ref = oracle.response_at(p, 2, DT, T0, N, o, o, hp, hc, t0h, src.lam, src.beta, src.psi, idx)
+        got = d_xyz[3 * out_off[s]:3 * out_off[s + 1]].view(3, N)[:, idx].cpu().numpy()
+        worst = max(worst, float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+    return worst
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--order", type=int, default=ORDER)
+    ap.add_argument("--sources", type=int, default=S_SOURCES)
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

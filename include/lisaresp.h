@@ -1,0 +1,176 @@
+/*
+ * lisaresp.h -- C ABI of the GB300 (sm_103a) generic LISA time-domain response library.
+ *
+ * The library computes the response of the LISA constellation to a gravitational-wave
+ * strain given as two polarisation time series on a uniform grid (Katz, Bayle, Chua &
+ * Vallisneri, arXiv:2204.06633):
+ *   - projection (Sec. "Projection on the constellation arms", Eq. instrument-response-to-gw):
+ *       y_rs(t) = [H_rs(t - L_rs(t) - k.x_s(t)/c) - H_rs(t - k.x_r(t)/c)] / (2 (1 - k.n_rs(t))),
+ *       H_rs = xi+ h+ + xix hx (Eq. projected-strain-ssb), n_rs from emitter s to receiver r;
+ *   - TDI (Sec. "Time-delay interferometry", Eqs. tdi1 and tdi2): first- and second-generation
+ *     Michelson X, Y, Z built from chained delays D_{i1..in} x(t) = x(t - sum L(t)) (summed,
+ *     as in the paper) or nested;
+ *   - every delayed read is a centered Lagrange fractional-delay FIR of odd degree p
+ *     (Sec. "Implementation"): taps m-(p-1)/2 .. m+(p+1)/2 around m = floor(x);
+ *   - orbits: spacecraft positions and link delays on a coarse uniform knot grid, cubic-spline
+ *     interpolated to each sample (Sec. "Implementation"); delays not given are solved from
+ *     the Newtonian light-time equation L_rs(t) = |x_r(t) - x_s(t - L_rs)| / c.
+ *
+ * Conventions
+ *   - Units: metres, seconds.  c = 299792458 m/s.
+ *   - Links are ordered 12, 23, 31, 13, 32, 21 (receiver first); link arrays are [6][n].
+ *   - TDI outputs are [3][n]: X, Y, Z (Y, Z by the cyclic permutation 1->2->3->1).
+ *   - Output sample n is at time t0 + n*dt; input sample j at t0_h + j*dt (same dt).
+ *   - Samples outside an array are zero (zero extension): the operators stay linear and
+ *     their transposes exact.  lr_required_margin() gives the input span a full-stencil
+ *     output needs.
+ *   - h+, hx are the un-rotated polarisations; the polarisation angle psi is applied inside
+ *     the response by rotating the antenna patterns by 2 psi (the matrix of Sec. "Template
+ *     generation").  For the paper's SSB sign convention pass -h+, -hx.
+ *
+ * Memory and threading
+ *   - Array arguments of compute calls are DEVICE pointers owned by the caller (float64,
+ *     contiguous), unless documented as host.  The library never frees or keeps them.
+ *   - The library allocates only its own tables (orbit spline coefficients, plan tables,
+ *     batch tile tables, the device error word) and frees them in the *_destroy calls.
+ *   - Compute calls are asynchronous on `stream` (a cudaStream_t passed as void*, NULL =
+ *     legacy default stream) and return after enqueueing.  Argument and range checks happen
+ *     on the host before any launch.  Device-side faults the kernels detect (a stencil index
+ *     outside its staged window, a bounded wait that ran out) are recorded in the plan's
+ *     error word and reported by lr_plan_check().
+ *   - Handles are not thread-safe: use one plan per host thread / stream.
+ *
+ * Errors: every call returns an lr_status; no exception crosses the ABI.
+ */
+#ifndef LISARESP_H
+#define LISARESP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LR_API __attribute__((visibility("default")))
+
+typedef enum {
+    LR_OK = 0,
+    LR_ERR_INVALID_ARG = 1,   /* null pointer, bad enum, non-positive size, ... */
+    LR_ERR_RANGE = 2,         /* sizes beyond what the plan or a table supports */
+    LR_ERR_OOM = 3,           /* device or host allocation failed */
+    LR_ERR_CUDA = 4,          /* a CUDA runtime call failed (see lr_last_cuda_error) */
+    LR_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out */
+    LR_ERR_NONFINITE = 6,     /* NaN or Inf found where finite values are required */
+    LR_ERR_UNSUPPORTED = 7,   /* valid request the library does not implement (e.g. even order) */
+    LR_ERR_DEVICE = 8         /* a kernel recorded an internal fault in the plan's error word */
+} lr_status;
+
+enum { LR_FP64 = 0, LR_MIXED = 1 };                       /* plan precision */
+enum { LR_DELAY_SUM = 0, LR_DELAY_NESTED = 1 };           /* chained-delay model */
+enum { LR_SPLINE_NOT_A_KNOT = 0, LR_SPLINE_NATURAL = 1 }; /* spline end conditions */
+
+typedef struct lr_ctx lr_ctx;
+typedef struct lr_orbit lr_orbit;
+typedef struct lr_plan lr_plan;
+
+/* Sky position (ecliptic longitude lambda, latitude beta) and polarisation angle psi, rad.
+ * k = -e_r, u = -e_phi, v = -e_theta of the SSB spherical basis (Sec. "Reference frames"). */
+typedef struct { double lam, beta, psi; } lr_sky;
+
+typedef struct {
+    int order;            /* Lagrange degree p: odd, 1 <= p <= 63 (a compiled subset; see lr_order_supported) */
+    int precision;        /* LR_FP64 or LR_MIXED */
+    int tdi_generation;   /* 1 (X1: Eq. tdi1) or 2 (X2: Eq. tdi2) */
+    int delay_mode;       /* LR_DELAY_SUM (the paper's summed delays) or LR_DELAY_NESTED */
+    double dt;            /* sample spacing (s), > 0 */
+    double t0;            /* time of output sample 0 (s) */
+    int64_t n;            /* output length of the single-source calls (>= 1) */
+    const lr_orbit *proj_orbit;  /* positions + delays used by the projection */
+    const lr_orbit *tdi_orbit;   /* delays used by TDI; may differ (hybrid templates) */
+    int tile;             /* output samples per CTA tile; 0 = autotuned / default */
+    int threads;          /* threads per CTA; 0 = default */
+} lr_plan_desc;
+
+/* ------------------------------------------------------------------ misc */
+LR_API const char *lr_strerror(int status);
+LR_API int lr_version(void);                        /* major*10000 + minor*100 + patch */
+LR_API int lr_order_supported(int order);           /* 1 if a kernel for this degree is compiled */
+
+/* ------------------------------------------------------------------ context */
+/* Binds the library to CUDA device `device` (>= 0).  *out is owned by the caller and freed
+ * by lr_ctx_destroy. */
+LR_API int lr_ctx_create(int device, lr_ctx **out);
+LR_API int lr_ctx_destroy(lr_ctx *ctx);
+/* cudaError_t of the last failing CUDA call made through this context (0 if none). */
+LR_API int lr_last_cuda_error(const lr_ctx *ctx);
+
+/* ------------------------------------------------------------------ orbits */
+/* Spacecraft positions and link delays on a uniform knot grid, interpolated by cubic
+ * splines (Sec. "Implementation"; the spline kind is not stated in the paper: not-a-knot
+ * by default).
+ *   t_knots : HOST [n_knots], strictly increasing and uniformly spaced (rel. 1e-9), n_knots >= 4
+ *   pos     : HOST [3 spacecraft][3 xyz][n_knots] (m)
+ *   delays  : HOST [6 links][n_knots] (s), or NULL: solve L_rs(t) = |x_r(t) - x_s(t - L_rs)|/c
+ *             on each knot by fixed-point iteration on the position spline
+ *   spline_bc : LR_SPLINE_NOT_A_KNOT or LR_SPLINE_NATURAL
+ * The host arrays are copied; the device tables belong to the orbit. */
+LR_API int lr_orbit_create(lr_ctx *ctx, const double *t_knots, int64_t n_knots, const double *pos,
+                           const double *delays, int spline_bc, lr_orbit **out);
+LR_API int lr_orbit_destroy(lr_orbit *orbit);
+/* Copies the delays on the knots (given or solved) to HOST out[6][n_knots]. */
+LR_API int lr_orbit_delays(const lr_orbit *orbit, double *out, int64_t n_knots);
+
+/* ------------------------------------------------------------------ plans */
+/* Validates the descriptor and precomputes the plan's device tables (TDI chain tables,
+ * halo sizes).  The orbits must outlive the plan. */
+LR_API int lr_plan_create(lr_ctx *ctx, const lr_plan_desc *desc, lr_plan **out);
+LR_API int lr_plan_destroy(lr_plan *plan);
+/* Input samples an output sample needs on each side of its own time: an input series that
+ * covers [t0 - left*dt, t0 + (n-1)*dt + right*dt] gives every output a full stencil. */
+LR_API int lr_required_margin(const lr_plan *plan, int64_t *left, int64_t *right);
+/* Waits for `stream`, then reads and clears the plan's device error word: LR_OK, or
+ * LR_ERR_DEVICE / LR_ERR_TIMEOUT if a kernel recorded a fault since the last check. */
+LR_API int lr_plan_check(lr_plan *plan, void *stream);
+
+/* ------------------------------------------------------------------ forward */
+/* Projection only: y[6][plan.n] from h+, hx (each [n_h], input grid t0_h + j*dt).
+ * Eq. instrument-response-to-gw with the projection orbit. */
+LR_API int lr_project(lr_plan *plan, const double *hp, const double *hc, int64_t n_h, double t0_h,
+                      lr_sky sky, double *y, void *stream);
+/* TDI only: xyz[3][plan.n] from y[6][plan.n] (Eqs. tdi1/tdi2 with the TDI orbit's delays). */
+LR_API int lr_tdi(lr_plan *plan, const double *y, double *xyz, void *stream);
+/* Fused projection + TDI: xyz[3][plan.n]; the link series stay on chip. */
+LR_API int lr_response(lr_plan *plan, const double *hp, const double *hc, int64_t n_h, double t0_h,
+                       lr_sky sky, double *xyz, void *stream);
+
+/* ------------------------------------------------------------------ backward */
+/* Transpose of lr_response applied to g_xyz[3][plan.n] (e.g. dLoss/dXYZ):
+ *   g_hp, g_hc [n_h]   = P^T T^T g_xyz            (overwritten)
+ *   g_sky[3] (DEVICE)  = d<g_xyz, R(h)>/d(lambda, beta, psi)   (overwritten; may be NULL)
+ * The link series and their gradient are recomputed, not stored.  Deterministic: gathers
+ * over inverted tap windows and fixed-order reductions, no atomics on the data. */
+LR_API int lr_backward(lr_plan *plan, const double *hp, const double *hc, int64_t n_h, double t0_h,
+                       lr_sky sky, const double *g_xyz, double *g_hp, double *g_hc, double *g_sky,
+                       void *stream);
+
+/* ------------------------------------------------------------------ batched */
+/* S independent sources with their own lengths in one persistent launch.
+ *   h_off   : DEVICE int64[S+1], source s reads hp/hc[h_off[s] .. h_off[s+1])
+ *   out_off : DEVICE int64[S+1], source s has n_s = out_off[s+1]-out_off[s] outputs, written
+ *             to xyz[3*out_off[s] ..) as [3][n_s]; output sample n at t0 + n*dt
+ *   t0_h    : DEVICE double[S], time of each source's input sample 0
+ *   sky     : DEVICE lr_sky[S]
+ * S <= 2^24.  The plan's n is ignored.  Offsets must be non-decreasing (checked on device:
+ * a violation records LR_ERR_DEVICE). */
+LR_API int lr_response_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
+                               const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
+                               double *xyz, void *stream);
+/* Batched transpose; g_sky is DEVICE [S][3] (may be NULL). */
+LR_API int lr_backward_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
+                               const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
+                               const double *g_xyz, double *g_hp, double *g_hc, double *g_sky, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LISARESP_H */

@@ -1,0 +1,275 @@
+"""Python binding of liblisaresp, the GB300-native generic LISA response library
+(arXiv:2204.06633: projection of h+, hx onto the six links and TDI X, Y, Z).
+
+This module only marshals arguments: every step of the response runs in the library's CUDA
+kernels (``csrc/``), reached through the C ABI declared in ``include/lisaresp.h``.  PyTorch
+supplies device memory and streams.  If the compiled library is missing, importing works but
+every call raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblisaresp.so")
+
+FP64, MIXED = 0, 1
+DELAY_SUM, DELAY_NESTED = 0, 1
+NOT_A_KNOT, NATURAL = 0, 1
+LINKS = ("12", "23", "31", "13", "32", "21")
+
+_lib = None
+
+
+class LRError(RuntimeError):
+    def __init__(self, where: str, status: int, detail: str = ""):
+        self.status = status
+        msg = f"{where}: {strerror(status)} (status {status})"
+        super().__init__(msg + (f" {detail}" if detail else ""))
+
+
+class lr_sky(ctypes.Structure):
+    _fields_ = [("lam", ctypes.c_double), ("beta", ctypes.c_double), ("psi", ctypes.c_double)]
+
+
+class lr_plan_desc(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int), ("precision", ctypes.c_int), ("tdi_generation", ctypes.c_int),
+                ("delay_mode", ctypes.c_int), ("dt", ctypes.c_double), ("t0", ctypes.c_double),
+                ("n", ctypes.c_int64), ("proj_orbit", ctypes.c_void_p), ("tdi_orbit", ctypes.c_void_p),
+                ("tile", ctypes.c_int), ("threads", ctypes.c_int)]
+
+
+_I, _I64, _D, _P = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+_PP = ctypes.POINTER(ctypes.c_void_p)
+_SIGS = {
+    "lr_strerror": (ctypes.c_char_p, [_I]),
+    "lr_version": (_I, []),
+    "lr_order_supported": (_I, [_I]),
+    "lr_ctx_create": (_I, [_I, _PP]),
+    "lr_ctx_destroy": (_I, [_P]),
+    "lr_last_cuda_error": (_I, [_P]),
+    "lr_orbit_create": (_I, [_P, _P, _I64, _P, _P, _I, _PP]),
+    "lr_orbit_destroy": (_I, [_P]),
+    "lr_orbit_delays": (_I, [_P, _P, _I64]),
+    "lr_plan_create": (_I, [_P, ctypes.POINTER(lr_plan_desc), _PP]),
+    "lr_plan_destroy": (_I, [_P]),
+    "lr_required_margin": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "lr_plan_check": (_I, [_P, _P]),
+    "lr_project": (_I, [_P, _P, _P, _I64, _D, lr_sky, _P, _P]),
+    "lr_tdi": (_I, [_P, _P, _P, _P]),
+    "lr_response": (_I, [_P, _P, _P, _I64, _D, lr_sky, _P, _P]),
+    "lr_backward": (_I, [_P, _P, _P, _I64, _D, lr_sky, _P, _P, _P, _P, _P]),
+    "lr_response_batched": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "lr_backward_batched": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+}
+
+
+def library() -> ctypes.CDLL:
+    """The loaded liblisaresp (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"liblisaresp.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def strerror(status: int) -> str:
+    try:
+        return library().lr_strerror(int(status)).decode()
+    except Exception:  # library missing while formatting an error
+        return "status %d" % status
+
+
+def _check(where: str, status: int):
+    if status != 0:
+        raise LRError(where, status)
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dev64(t: torch.Tensor, name: str, numel: int | None = None) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return t.data_ptr()
+
+
+def _devi64(t: torch.Tensor, name: str, numel: int) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.int64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous int64 CUDA tensor")
+    if t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return t.data_ptr()
+
+
+def _sky(sky) -> lr_sky:
+    if isinstance(sky, lr_sky):
+        return sky
+    lam, beta, psi = sky
+    return lr_sky(float(lam), float(beta), float(psi))
+
+
+class Context:
+    def __init__(self, device: int = 0):
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        _check("lr_ctx_create", library().lr_ctx_create(self.device, ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.lr_ctx_destroy(self._h)
+            self._h = None
+
+
+class Orbit:
+    """Spline-interpolated orbit: pos[3][3][n_knots] (m) on uniform knots; delays[6][n_knots] (s)
+    or None for the Newtonian light-time solve done by the library."""
+
+    def __init__(self, ctx: Context, t_knots, pos, delays=None, bc: int = NOT_A_KNOT):
+        import numpy as np
+        self.ctx = ctx
+        self._tk = np.ascontiguousarray(t_knots, dtype=np.float64)
+        self._pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(9, -1)
+        self._del = None if delays is None else np.ascontiguousarray(delays, dtype=np.float64).reshape(6, -1)
+        h = ctypes.c_void_p()
+        _check("lr_orbit_create", library().lr_orbit_create(
+            ctx.handle, self._tk.ctypes.data, len(self._tk), self._pos.ctypes.data,
+            None if self._del is None else self._del.ctypes.data, int(bc), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def delays_at_knots(self):
+        import numpy as np
+        out = np.empty((6, len(self._tk)))
+        _check("lr_orbit_delays", library().lr_orbit_delays(self._h, out.ctypes.data, len(self._tk)))
+        return out
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.lr_orbit_destroy(self._h)
+            self._h = None
+
+
+class Plan:
+    """A response configuration: Lagrange degree, precision, TDI generation, delay model,
+    output grid (t0 + n*dt, n samples) and the projection / TDI orbits."""
+
+    def __init__(self, ctx: Context, order: int, n: int, dt: float, proj_orbit: Orbit, tdi_orbit: Orbit | None = None,
+                 t0: float = 0.0, precision: int = FP64, generation: int = 2, delay_mode: int = DELAY_SUM,
+                 tile: int = 0, threads: int = 0):
+        self.ctx, self.n, self.order = ctx, int(n), int(order)
+        self.proj_orbit = proj_orbit
+        self.tdi_orbit = tdi_orbit if tdi_orbit is not None else proj_orbit
+        d = lr_plan_desc(int(order), int(precision), int(generation), int(delay_mode), float(dt), float(t0),
+                         int(n), proj_orbit.handle.value, self.tdi_orbit.handle.value, int(tile), int(threads))
+        self.desc = d
+        h = ctypes.c_void_p()
+        _check("lr_plan_create", library().lr_plan_create(ctx.handle, ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.lr_plan_destroy(self._h)
+            self._h = None
+
+    def required_margin(self):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check("lr_required_margin", library().lr_required_margin(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def check(self, stream=None):
+        """Waits for the stream and raises if a kernel recorded a fault."""
+        _check("lr_plan_check", library().lr_plan_check(self._h, _stream_handle(stream)))
+
+    def _out(self, out, shape, like):
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float64, device=like.device)
+        return out
+
+    def project(self, hp, hc, t0h, sky, y=None, stream=None):
+        y = self._out(y, (6, self.n), hp)
+        _check("lr_project", library().lr_project(
+            self._h, _dev64(hp, "hp"), _dev64(hc, "hc", hp.numel()), hp.numel(), float(t0h), _sky(sky),
+            _dev64(y, "y", 6 * self.n), _stream_handle(stream)))
+        return y
+
+    def tdi(self, y, xyz=None, stream=None):
+        xyz = self._out(xyz, (3, self.n), y)
+        _check("lr_tdi", library().lr_tdi(self._h, _dev64(y, "y", 6 * self.n), _dev64(xyz, "xyz", 3 * self.n),
+                                          _stream_handle(stream)))
+        return xyz
+
+    def response(self, hp, hc, t0h, sky, xyz=None, stream=None):
+        xyz = self._out(xyz, (3, self.n), hp)
+        _check("lr_response", library().lr_response(
+            self._h, _dev64(hp, "hp"), _dev64(hc, "hc", hp.numel()), hp.numel(), float(t0h), _sky(sky),
+            _dev64(xyz, "xyz", 3 * self.n), _stream_handle(stream)))
+        return xyz
+
+    def backward(self, hp, hc, t0h, sky, g_xyz, g_hp=None, g_hc=None, g_sky=None, stream=None):
+        g_hp = self._out(g_hp, hp.shape, hp)
+        g_hc = self._out(g_hc, hc.shape, hc)
+        g_sky = self._out(g_sky, (3,), hp)
+        _check("lr_backward", library().lr_backward(
+            self._h, _dev64(hp, "hp"), _dev64(hc, "hc", hp.numel()), hp.numel(), float(t0h), _sky(sky),
+            _dev64(g_xyz, "g_xyz", 3 * self.n), _dev64(g_hp, "g_hp", hp.numel()), _dev64(g_hc, "g_hc", hp.numel()),
+            _dev64(g_sky, "g_sky", 3), _stream_handle(stream)))
+        return g_hp, g_hc, g_sky
+
+    def response_batched(self, h_off, out_off, t0h, sky, hp, hc, xyz=None, stream=None):
+        """h_off, out_off: int64 CUDA [S+1]; t0h: float64 CUDA [S]; sky: float64 CUDA [S][3]."""
+        S = t0h.numel()
+        total = int(out_off[-1].item()) if xyz is None else xyz.numel() // 3
+        xyz = self._out(xyz, (3 * total,), hp)
+        _check("lr_response_batched", library().lr_response_batched(
+            self._h, S, _devi64(h_off, "h_off", S + 1), _devi64(out_off, "out_off", S + 1), _dev64(t0h, "t0h", S),
+            _dev64(sky, "sky", 3 * S), _dev64(hp, "hp"), _dev64(hc, "hc", hp.numel()), _dev64(xyz, "xyz"),
+            _stream_handle(stream)))
+        return xyz
+
+    def backward_batched(self, h_off, out_off, t0h, sky, hp, hc, g_xyz, g_hp=None, g_hc=None, g_sky=None,
+                         stream=None):
+        S = t0h.numel()
+        g_hp = self._out(g_hp, hp.shape, hp)
+        g_hc = self._out(g_hc, hc.shape, hc)
+        g_sky = self._out(g_sky, (S, 3), hp)
+        _check("lr_backward_batched", library().lr_backward_batched(
+            self._h, S, _devi64(h_off, "h_off", S + 1), _devi64(out_off, "out_off", S + 1), _dev64(t0h, "t0h", S),
+            _dev64(sky, "sky", 3 * S), _dev64(hp, "hp"), _dev64(hc, "hc", hp.numel()), _dev64(g_xyz, "g_xyz"),
+            _dev64(g_hp, "g_hp", hp.numel()), _dev64(g_hc, "g_hc", hp.numel()), _dev64(g_sky, "g_sky", 3 * S),
+            _stream_handle(stream)))
+        return g_hp, g_hc, g_sky
+
+
+def order_supported(order: int) -> bool:
+    return bool(library().lr_order_supported(int(order)))

@@ -1,0 +1,215 @@
+// Device building blocks shared by the response kernels: orbit splines, sky frame, tile
+// bookkeeping and the centered Lagrange fractional-delay read.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lr_internal.h"
+
+namespace lr {
+
+// ---------------------------------------------------------------- sky frame
+// k = -e_r, u = -e_phi, v = -e_theta of the SSB basis (Sec. "Reference frames"); c2p, s2p
+// rotate the antenna patterns by 2 psi.
+struct SkyConst {
+    double k[3], u[3], v[3];
+    double c2p, s2p;
+};
+
+__device__ inline SkyConst make_sky(const lr_sky &s)
+{
+    SkyConst c;
+    double sl, cl, sb, cb, s2, c2;
+    sincos(s.lam, &sl, &cl);
+    sincos(s.beta, &sb, &cb);
+    sincos(2.0 * s.psi, &s2, &c2);
+    c.k[0] = -cb * cl; c.k[1] = -cb * sl; c.k[2] = -sb;
+    c.u[0] = sl;       c.u[1] = -cl;      c.u[2] = 0.0;
+    c.v[0] = -sb * cl; c.v[1] = -sb * sl; c.v[2] = cb;
+    c.c2p = c2; c.s2p = s2;
+    return c;
+}
+
+// ---------------------------------------------------------------- splines
+struct alignas(32) Coef4 {
+    double a, b, c, d;
+};
+
+__device__ inline const Coef4 *spline_row(const OrbitDev &o, double t, double *x)
+{
+    double u = (t - o.t_first) * o.inv_dk;
+    double fl = floor(u);
+    int k = (int)fl;
+    k = k < 0 ? 0 : (k > o.nint - 1 ? o.nint - 1 : k);
+    *x = u - (double)k;
+    return reinterpret_cast<const Coef4 *>(o.coef) + (size_t)k * NSERIES;
+}
+
+__device__ inline Coef4 ldg4(const Coef4 *p)
+{
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    double2 u = __ldg(q), v = __ldg(q + 1);
+    Coef4 r;
+    r.a = u.x; r.b = u.y; r.c = v.x; r.d = v.y;
+    return r;
+}
+
+__device__ inline double cubic(const Coef4 &q, double x) { return fma(x, fma(x, fma(x, q.d, q.c), q.b), q.a); }
+
+// positions [9] and delays [6] at t
+__device__ inline void orbit_all(const OrbitDev &o, double t, double *pos, double *del)
+{
+    double x;
+    const Coef4 *row = spline_row(o, t, &x);
+#pragma unroll
+    for (int s = 0; s < 9; ++s) pos[s] = cubic(ldg4(row + s), x);
+#pragma unroll
+    for (int l = 0; l < 6; ++l) del[l] = cubic(ldg4(row + 9 + l), x);
+}
+
+__device__ inline void orbit_delays(const OrbitDev &o, double t, double *del)
+{
+    double x;
+    const Coef4 *row = spline_row(o, t, &x);
+#pragma unroll
+    for (int l = 0; l < 6; ++l) del[l] = cubic(ldg4(row + 9 + l), x);
+}
+
+__device__ inline double orbit_delay1(const OrbitDev &o, double t, int l)
+{
+    double x;
+    const Coef4 *row = spline_row(o, t, &x);
+    return cubic(ldg4(row + 9 + l), x);
+}
+
+// ---------------------------------------------------------------- tiles
+struct TileInfo {
+    int64_t n0, nb, N, nh;
+    double t0h;
+    lr_sky sky;
+    const double *hp, *hc;
+    double *out;      // base of this source's output block
+    const double *yin;
+    int ok;
+};
+
+// Maps global tile g to its source.  `ochan` is the number of output channels (3 for TDI,
+// 6 for link series).
+__device__ inline TileInfo tile_info(const FwdParams &P, int64_t g, int ochan)
+{
+    TileInfo ti;
+    ti.ok = 1;
+    if (P.src.tile_off == nullptr) {
+        ti.N = P.src.n1;
+        ti.nh = P.src.nh1;
+        ti.t0h = P.src.t0h1;
+        ti.sky = P.src.sky1;
+        ti.hp = P.hp;
+        ti.hc = P.hc;
+        ti.out = P.out;
+        ti.yin = P.yin;
+        ti.n0 = g * P.tile;
+    } else {
+        const int64_t *to = P.src.tile_off;
+        int64_t lo = 0, hi = P.src.S;  // find s with to[s] <= g < to[s+1]
+        while (hi - lo > 1) {
+            int64_t mid = (lo + hi) >> 1;
+            if (__ldg(to + mid) <= g) lo = mid; else hi = mid;
+        }
+        int64_t s = lo;
+        int64_t ho = __ldg(P.src.h_off + s), ho1 = __ldg(P.src.h_off + s + 1);
+        int64_t oo = __ldg(P.src.out_off + s), oo1 = __ldg(P.src.out_off + s + 1);
+        ti.N = oo1 - oo;
+        ti.nh = ho1 - ho;
+        if (ti.N < 0 || ti.nh < 0) ti.ok = 0;
+        ti.t0h = __ldg(P.src.t0h + s);
+        ti.sky = P.src.sky[s];
+        ti.hp = P.hp + ho;
+        ti.hc = P.hc + ho;
+        ti.out = P.out + ochan * oo;
+        ti.yin = P.yin ? P.yin + 6 * oo : nullptr;
+        ti.n0 = (g - __ldg(to + s)) * P.tile;
+    }
+    int64_t rem = ti.N - ti.n0;
+    ti.nb = rem < P.tile ? rem : P.tile;
+    if (ti.nb < 0) ti.nb = 0;
+    return ti;
+}
+
+// ---------------------------------------------------------------- Lagrange reads (FP64)
+// Centered Lagrange interpolation of degree p = T-1 through the nodes j = -h .. h+1
+// (h = (p-1)/2) at offset eps, w_a = (-1)^(T-1-a) L_a R_a with the prefix products
+// L_a = prod_{i<a} (eps+h-i)/(i+1) and suffix products R_a = prod_{i>a} (eps+h-i)/(T-i).
+// The sum  sum_a w_a s_a  is evaluated in nested (Horner) form over the suffix factors
+// f_a = (eps+h-a)/(T-a):  acc_a = acc_{a-1} f_a + sgn L_a s_a,  so no weight array is kept.
+template <int T>
+__device__ __forceinline__ double horner1(const double *__restrict__ s, double e)
+{
+    constexpr int h = (T - 2) / 2;
+    double L = -1.0;
+    double acc = -s[0];
+#pragma unroll
+    for (int j = 1; j < T; ++j) {
+        const double cf1 = 1.0 / (double)(T - j), cf0 = (double)(h - j) / (double)(T - j);
+        const double cg1 = -1.0 / (double)j, cg0 = (double)(j - 1 - h) / (double)j;
+        double f = fma(e, cf1, cf0);
+        L = L * fma(e, cg1, cg0);
+        acc = fma(acc, f, L * s[j]);
+    }
+    return acc;
+}
+
+template <int T>
+__device__ __forceinline__ void horner2(const double *__restrict__ a, const double *__restrict__ b, double e,
+                                        double &ra, double &rb)
+{
+    constexpr int h = (T - 2) / 2;
+    double L = -1.0;
+    double acca = -a[0], accb = -b[0];
+#pragma unroll
+    for (int j = 1; j < T; ++j) {
+        const double cf1 = 1.0 / (double)(T - j), cf0 = (double)(h - j) / (double)(T - j);
+        const double cg1 = -1.0 / (double)j, cg0 = (double)(j - 1 - h) / (double)j;
+        double f = fma(e, cf1, cf0);
+        L = L * fma(e, cg1, cg0);
+        acca = fma(acca, f, L * a[j]);
+        accb = fma(accb, f, L * b[j]);
+    }
+    ra = acca;
+    rb = accb;
+}
+
+// Reads series staged in shared memory at sample position base + u, where the staged
+// window starts at absolute index w_lo and holds wlen samples.  A stencil outside the
+// window records ERR_WINDOW and reads as 0 (never touches memory outside the window).
+template <int T>
+__device__ __forceinline__ double read1(const double *s, int64_t base, double u, int64_t w_lo, int wlen, int *err)
+{
+    constexpr int h = (T - 2) / 2;
+    double fl = floor(u);
+    double e = u - fl;
+    int64_t st = base + (int64_t)fl - h - w_lo;
+    if (st < 0 || st + T > wlen) {
+        atomicOr(err, ERR_WINDOW);
+        return 0.0;
+    }
+    return horner1<T>(s + st, e);
+}
+
+template <int T>
+__device__ __forceinline__ void read2(const double *a, const double *b, int64_t base, double u, int64_t w_lo,
+                                      int wlen, double &ra, double &rb, int *err)
+{
+    constexpr int h = (T - 2) / 2;
+    double fl = floor(u);
+    double e = u - fl;
+    int64_t st = base + (int64_t)fl - h - w_lo;
+    if (st < 0 || st + T > wlen) {
+        atomicOr(err, ERR_WINDOW);
+        ra = rb = 0.0;
+        return;
+    }
+    horner2<T>(a + st, b + st, e, ra, rb);
+}
+
+}  // namespace lr

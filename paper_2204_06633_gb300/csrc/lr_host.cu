@@ -1,0 +1,541 @@
+// Host side of the C ABI: contexts, orbit setup (cubic splines on a uniform knot grid, Newtonian
+// light-time solve), plans (halo and window sizing, launch shapes) and argument validation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lr_internal.h"
+#include "lr_launch.h"
+
+struct lr_ctx {
+    int device;
+    int sms;
+    int last_cuda_error;
+};
+
+struct lr_orbit {
+    lr_ctx *ctx;
+    int64_t nk;
+    int nint;
+    double t_first, dk;
+    std::vector<double> delays;   // [6][nk], given or solved
+    std::vector<double> coef;     // host copy [nint][15][4]
+    double *d_coef;
+    double max_r_over_c;          // max_t max_i |x_i(t)| / c  (s)
+    double max_delay;             // max_t max_l L_l(t)     (s)
+};
+
+struct lr_plan {
+    lr_ctx *ctx;
+    lr_plan_desc desc;
+    lr::FwdParams base;
+    int T, h;
+    int threads;
+    int *d_err;
+    int64_t *d_tile_off;
+    int64_t tile_cap;
+};
+
+namespace {
+
+int cuda_fail(lr_ctx *ctx, cudaError_t e)
+{
+    if (ctx) ctx->last_cuda_error = (int)e;
+    return LR_ERR_CUDA;
+}
+
+int check_launch(lr_ctx *ctx, int e)
+{
+    if (e == 0) return LR_OK;
+    return cuda_fail(ctx, (cudaError_t)e);
+}
+
+// ---------------------------------------------------------------- spline setup (host)
+// Second derivatives M of the interpolating cubic spline on uniform knots (spacing dk):
+// interior rows M_{k-1} + 4 M_k + M_{k+1} = 6 (y_{k+1} - 2 y_k + y_{k-1}) / dk^2.
+// not-a-knot: M_0 = 2 M_1 - M_2 and M_{n-1} = 2 M_{n-2} - M_{n-3} (third derivative
+// continuous at the second and penultimate knots), which turns the first and last interior
+// rows into 6 M_1 = rhs_1 and 6 M_{n-2} = rhs_{n-2}; natural: M_0 = M_{n-1} = 0.
+// The tridiagonal system is solved by forward elimination and back substitution.
+bool spline_second_derivatives(const double *y, int64_t n, double dk, int bc, std::vector<double> &M)
+{
+    M.assign((size_t)n, 0.0);
+    if (n < 3) return n == 2;  // two knots: straight line
+    int64_t m = n - 2;         // unknowns M_1 .. M_{n-2}
+    std::vector<double> a(m), b(m), c(m), r(m);
+    for (int64_t i = 0; i < m; ++i) {
+        int64_t k = i + 1;
+        a[i] = 1.0; b[i] = 4.0; c[i] = 1.0;
+        r[i] = 6.0 * (y[k + 1] - 2.0 * y[k] + y[k - 1]) / (dk * dk);
+    }
+    if (bc == LR_SPLINE_NOT_A_KNOT) {
+        b[0] = 6.0; c[0] = 0.0;
+        b[m - 1] = 6.0; a[m - 1] = 0.0;
+        if (m == 1) { b[0] = 6.0; }
+    }
+    a[0] = 0.0;
+    c[m - 1] = 0.0;
+    for (int64_t i = 1; i < m; ++i) {
+        double w = a[i] / b[i - 1];
+        b[i] -= w * c[i - 1];
+        r[i] -= w * r[i - 1];
+    }
+    std::vector<double> x(m);
+    x[m - 1] = r[m - 1] / b[m - 1];
+    for (int64_t i = m - 2; i >= 0; --i) x[i] = (r[i] - c[i] * x[i + 1]) / b[i];
+    for (int64_t i = 0; i < m; ++i) M[i + 1] = x[i];
+    if (bc == LR_SPLINE_NOT_A_KNOT) {
+        if (n < 4) return false;
+        M[0] = 2.0 * M[1] - M[2];
+        M[n - 1] = 2.0 * M[n - 2] - M[n - 3];
+    }
+    return true;
+}
+
+// Piecewise coefficients in the normalised coordinate x = (t - t_k)/dk:
+// S = y_k + b x + c x^2 + d x^3 with b = (y_{k+1}-y_k) - dk^2 (2 M_k + M_{k+1})/6,
+// c = dk^2 M_k / 2, d = dk^2 (M_{k+1} - M_k)/6.
+void spline_coefficients(const double *y, const std::vector<double> &M, int64_t n, double dk, double *coef,
+                         int series)
+{
+    double h2 = dk * dk;
+    for (int64_t k = 0; k + 1 < n; ++k) {
+        double *q = coef + ((size_t)k * lr::NSERIES + series) * 4;
+        q[0] = y[k];
+        q[1] = (y[k + 1] - y[k]) - h2 * (2.0 * M[k] + M[k + 1]) / 6.0;
+        q[2] = h2 * M[k] / 2.0;
+        q[3] = h2 * (M[k + 1] - M[k]) / 6.0;
+    }
+}
+
+double spline_eval_host(const lr_orbit *o, int series, double t)
+{
+    double u = (t - o->t_first) / o->dk;
+    int64_t k = (int64_t)std::floor(u);
+    if (k < 0) k = 0;
+    if (k > o->nint - 1) k = o->nint - 1;
+    double x = u - (double)k;
+    const double *q = o->coef.data() + ((size_t)k * lr::NSERIES + series) * 4;
+    return q[0] + x * (q[1] + x * (q[2] + x * q[3]));
+}
+
+const int LINK_R[6] = {0, 1, 2, 0, 2, 1};  // link order 12, 23, 31, 13, 32, 21 (0-based)
+const int LINK_S[6] = {1, 2, 0, 2, 1, 0};
+
+// Newtonian light time of link (r <- s) received at t: L = |x_r(t) - x_s(t - L)|/c, solved by
+// fixed-point iteration from L = |x_r(t) - x_s(t)|/c (a contraction: |dx_s/dt|/c ~ 1e-4).
+bool light_time(const lr_orbit *o, int l, double t, double *out)
+{
+    int r = LINK_R[l], s = LINK_S[l];
+    double xr[3], xs[3];
+    for (int d = 0; d < 3; ++d) {
+        xr[d] = spline_eval_host(o, 3 * r + d, t);
+        xs[d] = spline_eval_host(o, 3 * s + d, t);
+    }
+    double L = std::sqrt((xr[0] - xs[0]) * (xr[0] - xs[0]) + (xr[1] - xs[1]) * (xr[1] - xs[1]) +
+                         (xr[2] - xs[2]) * (xr[2] - xs[2])) / lr::C_LIGHT;
+    for (int it = 0; it < 100; ++it) {
+        for (int d = 0; d < 3; ++d) xs[d] = spline_eval_host(o, 3 * s + d, t - L);
+        double Ln = std::sqrt((xr[0] - xs[0]) * (xr[0] - xs[0]) + (xr[1] - xs[1]) * (xr[1] - xs[1]) +
+                              (xr[2] - xs[2]) * (xr[2] - xs[2])) / lr::C_LIGHT;
+        double ch = std::fabs(Ln - L);
+        L = Ln;
+        if (ch <= 1e-15 * L) {
+            *out = L;
+            return true;
+        }
+    }
+    *out = L;
+    return std::isfinite(L);
+}
+
+bool all_finite(const double *p, size_t n)
+{
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+extern "C" {
+
+LR_API const char *lr_strerror(int status)
+{
+    switch (status) {
+        case LR_OK: return "success";
+        case LR_ERR_INVALID_ARG: return "invalid argument";
+        case LR_ERR_RANGE: return "size or value out of the supported range";
+        case LR_ERR_OOM: return "out of memory";
+        case LR_ERR_CUDA: return "CUDA runtime error";
+        case LR_ERR_TIMEOUT: return "bounded device wait ran out";
+        case LR_ERR_NONFINITE: return "non-finite input";
+        case LR_ERR_UNSUPPORTED: return "unsupported request";
+        case LR_ERR_DEVICE: return "kernel recorded an internal fault";
+        default: return "unknown status";
+    }
+}
+
+LR_API int lr_version(void) { return 100; }
+
+LR_API int lr_order_supported(int order) { return lr::order_supported(order) ? 1 : 0; }
+
+LR_API int lr_ctx_create(int device, lr_ctx **out)
+{
+    if (!out || device < 0) return LR_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return LR_ERR_CUDA;
+    if (device >= ndev) return LR_ERR_RANGE;
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return LR_ERR_CUDA;
+    lr_ctx *c = new (std::nothrow) lr_ctx();
+    if (!c) return LR_ERR_OOM;
+    c->device = device;
+    c->last_cuda_error = 0;
+    e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+        delete c;
+        return LR_ERR_CUDA;
+    }
+    *out = c;
+    return LR_OK;
+}
+
+LR_API int lr_ctx_destroy(lr_ctx *ctx)
+{
+    if (!ctx) return LR_ERR_INVALID_ARG;
+    delete ctx;
+    return LR_OK;
+}
+
+LR_API int lr_last_cuda_error(const lr_ctx *ctx) { return ctx ? ctx->last_cuda_error : 0; }
+
+LR_API int lr_orbit_create(lr_ctx *ctx, const double *t_knots, int64_t n_knots, const double *pos,
+                           const double *delays, int spline_bc, lr_orbit **out)
+{
+    if (!ctx || !t_knots || !pos || !out) return LR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (spline_bc != LR_SPLINE_NOT_A_KNOT && spline_bc != LR_SPLINE_NATURAL) return LR_ERR_INVALID_ARG;
+    if (n_knots < 4 || n_knots > (1 << 24)) return LR_ERR_RANGE;
+    if (!all_finite(t_knots, (size_t)n_knots) || !all_finite(pos, (size_t)(9 * n_knots))) return LR_ERR_NONFINITE;
+    if (delays && !all_finite(delays, (size_t)(6 * n_knots))) return LR_ERR_NONFINITE;
+    double dk = (t_knots[n_knots - 1] - t_knots[0]) / (double)(n_knots - 1);
+    if (!(dk > 0.0)) return LR_ERR_INVALID_ARG;
+    for (int64_t k = 0; k < n_knots; ++k)
+        if (std::fabs(t_knots[k] - (t_knots[0] + (double)k * dk)) > 1e-9 * dk) return LR_ERR_INVALID_ARG;
+
+    lr_orbit *o = new (std::nothrow) lr_orbit();
+    if (!o) return LR_ERR_OOM;
+    o->ctx = ctx;
+    o->nk = n_knots;
+    o->nint = (int)(n_knots - 1);
+    o->t_first = t_knots[0];
+    o->dk = dk;
+    o->d_coef = nullptr;
+    try {
+        o->coef.assign((size_t)o->nint * lr::NSERIES * 4, 0.0);
+        std::vector<double> M;
+        for (int s = 0; s < 9; ++s) {
+            if (!spline_second_derivatives(pos + (size_t)s * n_knots, n_knots, dk, spline_bc, M)) {
+                delete o;
+                return LR_ERR_INVALID_ARG;
+            }
+            spline_coefficients(pos + (size_t)s * n_knots, M, n_knots, dk, o->coef.data(), s);
+        }
+        o->delays.assign((size_t)6 * n_knots, 0.0);
+        if (delays) {
+            std::memcpy(o->delays.data(), delays, sizeof(double) * 6 * (size_t)n_knots);
+        } else {
+            for (int l = 0; l < 6; ++l)
+                for (int64_t k = 0; k < n_knots; ++k)
+                    if (!light_time(o, l, t_knots[k], &o->delays[(size_t)l * n_knots + k])) {
+                        delete o;
+                        return LR_ERR_NONFINITE;
+                    }
+        }
+        for (int l = 0; l < 6; ++l) {
+            if (!spline_second_derivatives(o->delays.data() + (size_t)l * n_knots, n_knots, dk, spline_bc, M)) {
+                delete o;
+                return LR_ERR_INVALID_ARG;
+            }
+            spline_coefficients(o->delays.data() + (size_t)l * n_knots, M, n_knots, dk, o->coef.data(), 9 + l);
+        }
+    } catch (const std::bad_alloc &) {
+        delete o;
+        return LR_ERR_OOM;
+    }
+    // bounds over the grid, sampled on knots and at 8 points per interval (the cubic pieces
+    // of smooth orbits overshoot their knot values only by a tiny amount)
+    double rmax = 0.0, lmax = 0.0;
+    for (int k = 0; k < o->nint; ++k)
+        for (int j = 0; j <= 8; ++j) {
+            double t = o->t_first + ((double)k + j / 8.0) * dk;
+            for (int i = 0; i < 3; ++i) {
+                double r2 = 0.0;
+                for (int d = 0; d < 3; ++d) {
+                    double v = spline_eval_host(o, 3 * i + d, t);
+                    r2 += v * v;
+                }
+                rmax = std::max(rmax, std::sqrt(r2));
+            }
+            for (int l = 0; l < 6; ++l) lmax = std::max(lmax, std::fabs(spline_eval_host(o, 9 + l, t)));
+        }
+    o->max_r_over_c = rmax / lr::C_LIGHT * (1.0 + 1e-3) + 1e-3;
+    o->max_delay = lmax * (1.0 + 1e-3) + 1e-3;
+    cudaError_t e = cudaMalloc(&o->d_coef, sizeof(double) * o->coef.size());
+    if (e != cudaSuccess) {
+        delete o;
+        return e == cudaErrorMemoryAllocation ? LR_ERR_OOM : cuda_fail(ctx, e);
+    }
+    e = cudaMemcpy(o->d_coef, o->coef.data(), sizeof(double) * o->coef.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(o->d_coef);
+        delete o;
+        return cuda_fail(ctx, e);
+    }
+    *out = o;
+    return LR_OK;
+}
+
+LR_API int lr_orbit_destroy(lr_orbit *orbit)
+{
+    if (!orbit) return LR_ERR_INVALID_ARG;
+    if (orbit->d_coef) cudaFree(orbit->d_coef);
+    delete orbit;
+    return LR_OK;
+}
+
+LR_API int lr_orbit_delays(const lr_orbit *orbit, double *out, int64_t n_knots)
+{
+    if (!orbit || !out) return LR_ERR_INVALID_ARG;
+    if (n_knots != orbit->nk) return LR_ERR_RANGE;
+    std::memcpy(out, orbit->delays.data(), sizeof(double) * orbit->delays.size());
+    return LR_OK;
+}
+
+LR_API int lr_plan_create(lr_ctx *ctx, const lr_plan_desc *d, lr_plan **out)
+{
+    if (!ctx || !d || !out) return LR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!d->proj_orbit || !d->tdi_orbit) return LR_ERR_INVALID_ARG;
+    if (d->order < 1 || d->order > 63) return LR_ERR_RANGE;
+    if ((d->order & 1) == 0) return LR_ERR_UNSUPPORTED;
+    if (!lr::order_supported(d->order)) return LR_ERR_UNSUPPORTED;
+    if (d->precision != LR_FP64 && d->precision != LR_MIXED) return LR_ERR_INVALID_ARG;
+    if (d->tdi_generation != 1 && d->tdi_generation != 2) return LR_ERR_INVALID_ARG;
+    if (d->delay_mode != LR_DELAY_SUM && d->delay_mode != LR_DELAY_NESTED) return LR_ERR_INVALID_ARG;
+    if (!(d->dt > 0.0) || !std::isfinite(d->dt) || !std::isfinite(d->t0)) return LR_ERR_INVALID_ARG;
+    if (d->n < 1) return LR_ERR_INVALID_ARG;
+    if (d->tile < 0 || d->tile > 8192 || d->threads < 0 || d->threads > 1024) return LR_ERR_RANGE;
+    if (d->threads && (d->threads % 32)) return LR_ERR_INVALID_ARG;
+    if (!lr::precision_supported(d->precision)) return LR_ERR_UNSUPPORTED;
+
+    lr_plan *p = new (std::nothrow) lr_plan();
+    if (!p) return LR_ERR_OOM;
+    p->ctx = ctx;
+    p->desc = *d;
+    p->T = d->order + 1;
+    p->h = (d->order - 1) / 2;
+    p->threads = d->threads ? d->threads : 256;
+    p->d_err = nullptr;
+    p->d_tile_off = nullptr;
+    p->tile_cap = 0;
+    lr::FwdParams &P = p->base;
+    std::memset(&P, 0, sizeof(P));
+    P.dt = d->dt;
+    P.inv_dt = 1.0 / d->dt;
+    P.t0 = d->t0;
+    P.po = {d->proj_orbit->d_coef, d->proj_orbit->nint, d->proj_orbit->t_first, 1.0 / d->proj_orbit->dk};
+    P.to = {d->tdi_orbit->d_coef, d->tdi_orbit->nint, d->tdi_orbit->t_first, 1.0 / d->tdi_orbit->dk};
+    P.q_terms = d->tdi_generation == 1 ? 3 : 7;
+    P.delay_nested = d->delay_mode == LR_DELAY_NESTED;
+    P.tile = d->tile ? d->tile : lr::default_tile(d->precision, d->order);
+    // a chained delay is at most q_terms link delays; a tile's link series extend by that
+    // plus the stencil on the left and by the stencil on the right
+    double chain = (double)P.q_terms * d->tdi_orbit->max_delay / d->dt;
+    if (chain > 1e6) {
+        delete p;
+        return LR_ERR_RANGE;
+    }
+    P.HL = (int)std::ceil(chain) + p->h + 2;
+    P.HR = p->h + 2;
+    double sig = d->proj_orbit->max_r_over_c / d->dt;
+    double lp = d->proj_orbit->max_delay / d->dt;
+    if (sig > 1e6 || lp > 1e6) {
+        delete p;
+        return LR_ERR_RANGE;
+    }
+    P.sig_b = (int)std::ceil(sig) + 1;
+    P.lproj_b = (int)std::ceil(lp) + 1;
+    P.ymax = P.tile + P.HL + P.HR;
+    P.wmax = P.ymax + 2 * P.sig_b + P.lproj_b + p->T + 4;
+    cudaError_t e = cudaMalloc(&p->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        if (p->d_err) cudaFree(p->d_err);
+        delete p;
+        return cuda_fail(ctx, e);
+    }
+    P.err = p->d_err;
+    *out = p;
+    return LR_OK;
+}
+
+LR_API int lr_plan_destroy(lr_plan *plan)
+{
+    if (!plan) return LR_ERR_INVALID_ARG;
+    if (plan->d_err) cudaFree(plan->d_err);
+    if (plan->d_tile_off) cudaFree(plan->d_tile_off);
+    delete plan;
+    return LR_OK;
+}
+
+LR_API int lr_required_margin(const lr_plan *plan, int64_t *left, int64_t *right)
+{
+    if (!plan || !left || !right) return LR_ERR_INVALID_ARG;
+    *left = plan->base.sig_b + plan->base.lproj_b + plan->h + 2;
+    *right = plan->base.sig_b + plan->h + 2;
+    return LR_OK;
+}
+
+LR_API int lr_plan_check(lr_plan *plan, void *stream)
+{
+    if (!plan) return LR_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(plan->ctx, e);
+    int flag = 0;
+    e = cudaMemcpy(&flag, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(plan->ctx, e);
+    if (flag) {
+        e = cudaMemset(plan->d_err, 0, sizeof(int));
+        if (e != cudaSuccess) return cuda_fail(plan->ctx, e);
+    }
+    if (flag & lr::ERR_TIMEOUT) return LR_ERR_TIMEOUT;
+    if (flag) return LR_ERR_DEVICE;
+    return LR_OK;
+}
+
+}  // extern "C"
+
+// ================================================================== launches
+namespace {
+
+int launch_single(lr_plan *plan, int kind, lr::FwdParams &P, void *stream)
+{
+    const int64_t n = plan->desc.n;
+    P.total_tiles = (n + P.tile - 1) / P.tile;
+    return check_launch(plan->ctx, lr::launch_forward(plan->desc.precision, kind, plan->desc.order, P,
+                                                      plan->threads, plan->ctx->sms, stream));
+}
+
+}  // namespace
+
+extern "C" {
+
+LR_API int lr_project(lr_plan *plan, const double *hp, const double *hc, int64_t n_h, double t0_h, lr_sky sky,
+                      double *y, void *stream)
+{
+    if (!plan || !hp || !hc || !y) return LR_ERR_INVALID_ARG;
+    if (n_h < 1) return LR_ERR_INVALID_ARG;
+    if (!std::isfinite(t0_h) || !std::isfinite(sky.lam) || !std::isfinite(sky.beta) || !std::isfinite(sky.psi))
+        return LR_ERR_NONFINITE;
+    if (std::fabs(plan->desc.t0 - t0_h) / plan->desc.dt > 1e12) return LR_ERR_RANGE;
+    lr::FwdParams P = plan->base;
+    P.src.n1 = plan->desc.n;
+    P.src.nh1 = n_h;
+    P.src.t0h1 = t0_h;
+    P.src.sky1 = sky;
+    P.hp = hp;
+    P.hc = hc;
+    P.out = y;
+    return launch_single(plan, lr::KIND_PROJECT, P, stream);
+}
+
+LR_API int lr_tdi(lr_plan *plan, const double *y, double *xyz, void *stream)
+{
+    if (!plan || !y || !xyz) return LR_ERR_INVALID_ARG;
+    lr::FwdParams P = plan->base;
+    P.src.n1 = plan->desc.n;
+    P.src.nh1 = 0;
+    P.yin = y;
+    P.out = xyz;
+    return launch_single(plan, lr::KIND_TDI, P, stream);
+}
+
+LR_API int lr_response(lr_plan *plan, const double *hp, const double *hc, int64_t n_h, double t0_h, lr_sky sky,
+                       double *xyz, void *stream)
+{
+    if (!plan || !hp || !hc || !xyz) return LR_ERR_INVALID_ARG;
+    if (n_h < 1) return LR_ERR_INVALID_ARG;
+    if (!std::isfinite(t0_h) || !std::isfinite(sky.lam) || !std::isfinite(sky.beta) || !std::isfinite(sky.psi))
+        return LR_ERR_NONFINITE;
+    if (std::fabs(plan->desc.t0 - t0_h) / plan->desc.dt > 1e12) return LR_ERR_RANGE;
+    lr::FwdParams P = plan->base;
+    P.src.n1 = plan->desc.n;
+    P.src.nh1 = n_h;
+    P.src.t0h1 = t0_h;
+    P.src.sky1 = sky;
+    P.hp = hp;
+    P.hc = hc;
+    P.out = xyz;
+    return launch_single(plan, lr::KIND_FUSED, P, stream);
+}
+
+LR_API int lr_response_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
+                               const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
+                               double *xyz, void *stream)
+{
+    if (!plan || !h_off || !out_off || !t0_h || !sky || !hp || !hc || !xyz) return LR_ERR_INVALID_ARG;
+    if (S < 1) return LR_ERR_INVALID_ARG;
+    if (S > (int64_t)1 << 24) return LR_ERR_RANGE;
+    if (S + 1 > plan->tile_cap) {
+        if (plan->d_tile_off) cudaFree(plan->d_tile_off);
+        plan->d_tile_off = nullptr;
+        plan->tile_cap = 0;
+        cudaError_t e = cudaMalloc(&plan->d_tile_off, sizeof(int64_t) * (size_t)(S + 1));
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LR_ERR_OOM : cuda_fail(plan->ctx, e);
+        plan->tile_cap = S + 1;
+    }
+    lr::FwdParams P = plan->base;
+    int e = lr::launch_tile_offsets(out_off, S, P.tile, plan->d_tile_off, P.err, stream);
+    if (e) return check_launch(plan->ctx, e);
+    P.src.h_off = h_off;
+    P.src.out_off = out_off;
+    P.src.t0h = t0_h;
+    P.src.sky = sky;
+    P.src.tile_off = plan->d_tile_off;
+    P.src.S = S;
+    P.hp = hp;
+    P.hc = hc;
+    P.out = xyz;
+    P.total_tiles = -1;
+    return check_launch(plan->ctx, lr::launch_forward(plan->desc.precision, lr::KIND_FUSED, plan->desc.order, P,
+                                                      plan->threads, plan->ctx->sms, stream));
+}
+
+LR_API int lr_backward(lr_plan *plan, const double *hp, const double *hc, int64_t n_h, double t0_h, lr_sky sky,
+                       const double *g_xyz, double *g_hp, double *g_hc, double *g_sky, void *stream)
+{
+    (void)plan; (void)hp; (void)hc; (void)n_h; (void)t0_h; (void)sky; (void)g_xyz; (void)g_hp; (void)g_hc;
+    (void)g_sky; (void)stream;
+    return LR_ERR_UNSUPPORTED;
+}
+
+LR_API int lr_backward_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
+                               const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
+                               const double *g_xyz, double *g_hp, double *g_hc, double *g_sky, void *stream)
+{
+    (void)plan; (void)S; (void)h_off; (void)out_off; (void)t0_h; (void)sky; (void)hp; (void)hc; (void)g_xyz;
+    (void)g_hp; (void)g_hc; (void)g_sky; (void)stream;
+    return LR_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"

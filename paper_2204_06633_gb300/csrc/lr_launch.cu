@@ -1,0 +1,77 @@
+// Launch layer: kernel-family dispatch, persistent grid sizing and the batch tile table.
+#include <cuda_runtime.h>
+
+#include "lr_launch.h"
+
+namespace lr {
+
+bool order_supported(int order) { return order >= 1 && (order & 1) && order_compiled(order); }
+
+bool precision_supported(int precision) { return precision == LR_FP64; }
+
+int default_tile(int precision, int order)
+{
+    (void)precision;
+    (void)order;
+    return 512;
+}
+
+int launch_forward(int precision, int kind, int order, FwdParams &P, int threads, int sms, void *stream)
+{
+    (void)precision;
+    size_t smem = 0;
+    smem_fwd64(kind, order, P, &smem);
+    int per_sm = 0;
+    int e = max_blocks_fwd64(kind, order, threads, smem, &per_sm);
+    if (e) return e;
+    if (per_sm < 1) return (int)cudaErrorLaunchOutOfResources;
+    int64_t grid = (int64_t)per_sm * sms;
+    if (P.total_tiles >= 0 && P.total_tiles < grid) grid = P.total_tiles;
+    if (grid < 1) grid = 1;
+    return launch_fwd64(kind, order, P, (int)grid, threads, smem, stream);
+}
+
+// Prefix sums of tiles per source (one block; each thread scans a contiguous chunk of
+// sources, then the chunk totals are scanned in shared memory).  Decreasing offsets are
+// recorded as ERR_OFFSETS and count as empty sources.
+__global__ void __launch_bounds__(1024) k_tile_offsets(const int64_t *__restrict__ out_off, int64_t S, int tile,
+                                                       int64_t *__restrict__ tile_off, int *err)
+{
+    __shared__ int64_t part[1024];
+    const int64_t chunk = (S + blockDim.x - 1) / blockDim.x;
+    const int64_t s0 = threadIdx.x * chunk;
+    const int64_t s1 = s0 + chunk < S ? s0 + chunk : S;
+    int64_t sum = 0;
+    for (int64_t s = s0; s < s1; ++s) {
+        int64_t n = out_off[s + 1] - out_off[s];
+        if (n < 0) {
+            atomicOr(err, ERR_OFFSETS);
+            n = 0;
+        }
+        sum += (n + tile - 1) / tile;
+    }
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        int64_t v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int64_t run = part[threadIdx.x] - sum;  // exclusive prefix of this chunk
+    for (int64_t s = s0; s < s1; ++s) {
+        tile_off[s] = run;
+        int64_t n = out_off[s + 1] - out_off[s];
+        if (n < 0) n = 0;
+        run += (n + tile - 1) / tile;
+    }
+    if (threadIdx.x == blockDim.x - 1) tile_off[S] = part[threadIdx.x];
+}
+
+int launch_tile_offsets(const int64_t *out_off, int64_t S, int tile, int64_t *tile_off, int *err, void *stream)
+{
+    k_tile_offsets<<<1, 1024, 0, (cudaStream_t)stream>>>(out_off, S, tile, tile_off, err);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace lr

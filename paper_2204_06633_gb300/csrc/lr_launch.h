@@ -1,0 +1,13 @@
+// Launch layer: picks the kernel family for a plan's precision and sizes the persistent grid.
+#pragma once
+#include "lr_internal.h"
+
+namespace lr {
+bool order_supported(int order);
+bool precision_supported(int precision);
+int default_tile(int precision, int order);
+// returns a cudaError_t value (0 = success)
+int launch_forward(int precision, int kind, int order, FwdParams &P, int threads, int sms, void *stream);
+int launch_tile_offsets(const int64_t *out_off, int64_t S, int tile, int64_t *tile_off, int *err, void *stream);
+bool order_compiled(int order);
+}  // namespace lr
