@@ -154,6 +154,38 @@ bool light_time(const lr_orbit *o, int l, double t, double *out)
     return std::isfinite(L);
 }
 
+// Inverse of the Vandermonde matrix V_ik = c_i^k of the four Chebyshev nodes
+// c_i = cos((2i+1) pi / 8): row k maps node values to the coefficient of s^k of the cubic
+// through them (Gauss-Jordan elimination with partial pivoting).
+void chebyshev_inverse(double out[4][4])
+{
+    double a[4][8];
+    for (int i = 0; i < 4; ++i) {
+        double c = std::cos((2.0 * i + 1.0) * 3.14159265358979323846 / 8.0), pw = 1.0;
+        for (int k = 0; k < 4; ++k) {
+            a[i][k] = pw;
+            pw *= c;
+            a[i][4 + k] = i == k ? 1.0 : 0.0;
+        }
+    }
+    for (int col = 0; col < 4; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 4; ++r)
+            if (std::fabs(a[r][col]) > std::fabs(a[piv][col])) piv = r;
+        for (int k = 0; k < 8; ++k) std::swap(a[col][k], a[piv][k]);
+        double d = a[col][col];
+        for (int k = 0; k < 8; ++k) a[col][k] /= d;
+        for (int r = 0; r < 4; ++r)
+            if (r != col) {
+                double f = a[r][col];
+                for (int k = 0; k < 8; ++k) a[r][k] -= f * a[col][k];
+            }
+    }
+    // a[:, 4:] = V^{-1}: coefficient k = sum_i V^{-1}[k][i] y_i
+    for (int k = 0; k < 4; ++k)
+        for (int i = 0; i < 4; ++i) out[k][i] = a[k][4 + i];
+}
+
 bool all_finite(const double *p, size_t n)
 {
     for (size_t i = 0; i < n; ++i)
@@ -357,7 +389,7 @@ LR_API int lr_plan_create(lr_ctx *ctx, const lr_plan_desc *d, lr_plan **out)
     P.to = {d->tdi_orbit->d_coef, d->tdi_orbit->nint, d->tdi_orbit->t_first, 1.0 / d->tdi_orbit->dk};
     P.q_terms = d->tdi_generation == 1 ? 3 : 7;
     P.delay_nested = d->delay_mode == LR_DELAY_NESTED;
-    P.tile = d->tile ? d->tile : lr::default_tile(d->precision, d->order);
+    P.tile = d->tile;
     // a chained delay is at most q_terms link delays; a tile's link series extend by that
     // plus the stencil on the left and by the stencil on the right
     double chain = (double)P.q_terms * d->tdi_orbit->max_delay / d->dt;
@@ -367,6 +399,11 @@ LR_API int lr_plan_create(lr_ctx *ctx, const lr_plan_desc *d, lr_plan **out)
     }
     P.HL = (int)std::ceil(chain) + p->h + 2;
     P.HR = p->h + 2;
+    if (P.tile == 0) {
+        // mixed: the tile plus its link halo fills exactly one pass of the CTA's threads
+        P.tile = d->precision == LR_MIXED ? std::max(32, lr::MIXED_THREADS - P.HL - P.HR)
+                                          : lr::default_tile(d->precision, d->order);
+    }
     double sig = d->proj_orbit->max_r_over_c / d->dt;
     double lp = d->proj_orbit->max_delay / d->dt;
     if (sig > 1e6 || lp > 1e6) {
@@ -377,6 +414,19 @@ LR_API int lr_plan_create(lr_ctx *ctx, const lr_plan_desc *d, lr_plan **out)
     P.lproj_b = (int)std::ceil(lp) + 1;
     P.ymax = P.tile + P.HL + P.HR;
     P.wmax = P.ymax + 2 * P.sig_b + P.lproj_b + p->T + 4;
+    if (d->precision == LR_MIXED) {
+        // the mixed kernels re-expand the orbit cubics over a tile: a tile's link span must fit
+        // in two knot intervals, and the chained delays are summed, not nested
+        if (d->delay_mode == LR_DELAY_NESTED) {
+            delete p;
+            return LR_ERR_UNSUPPORTED;
+        }
+        if ((double)P.ymax * d->dt >= d->proj_orbit->dk || (double)P.tile * d->dt >= d->tdi_orbit->dk) {
+            delete p;
+            return LR_ERR_RANGE;
+        }
+    }
+    chebyshev_inverse(P.cheb);
     cudaError_t e = cudaMalloc(&p->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
     if (e != cudaSuccess) {

@@ -65,6 +65,7 @@ struct FwdParams {
     double *out;            // y [6][n] or xyz [3][n]
     int *err;               // device error word
     int64_t total_tiles;    // >= 0 single source; -1: read src.tile_off[S]
+    double cheb[4][4];      // monomial coefficients of the cubic through 4 Chebyshev nodes on [-1, 1]
 };
 
 // error-word bits
@@ -79,5 +80,10 @@ namespace lr {
 int launch_fwd64(int kind, int order, const FwdParams &P, int grid, int threads, size_t smem, void *stream);
 int smem_fwd64(int kind, int order, const FwdParams &P, size_t *smem);
 int max_blocks_fwd64(int kind, int order, int threads, size_t smem, int *blocks);
+int launch_fwdmx(int kind, int order, const FwdParams &P, int grid, int threads, size_t smem, void *stream);
+int smem_fwdmx(int kind, int order, const FwdParams &P, size_t *smem);
+int max_blocks_fwdmx(int kind, int order, int threads, size_t smem, int *blocks);
+bool order_compiled_mx(int order);
+constexpr int MIXED_THREADS = 256;  // the mixed kernels' per-tile setup assigns work by thread index
 enum { KIND_PROJECT = 0, KIND_TDI = 1, KIND_FUSED = 2 };
 }  // namespace lr

@@ -5,30 +5,31 @@
 
 namespace lr {
 
-bool order_supported(int order) { return order >= 1 && (order & 1) && order_compiled(order); }
+bool order_supported(int order) { return order >= 1 && (order & 1) && order_compiled(order) && order_compiled_mx(order); }
 
-bool precision_supported(int precision) { return precision == LR_FP64; }
+bool precision_supported(int precision) { return precision == LR_FP64 || precision == LR_MIXED; }
 
 int default_tile(int precision, int order)
 {
-    (void)precision;
     (void)order;
-    return 512;
+    return precision == LR_MIXED ? 256 : 512;
 }
 
 int launch_forward(int precision, int kind, int order, FwdParams &P, int threads, int sms, void *stream)
 {
-    (void)precision;
+    const bool mx = precision == LR_MIXED;
+    if (mx) threads = MIXED_THREADS;
     size_t smem = 0;
-    smem_fwd64(kind, order, P, &smem);
+    if (mx) smem_fwdmx(kind, order, P, &smem); else smem_fwd64(kind, order, P, &smem);
     int per_sm = 0;
-    int e = max_blocks_fwd64(kind, order, threads, smem, &per_sm);
+    int e = mx ? max_blocks_fwdmx(kind, order, threads, smem, &per_sm) : max_blocks_fwd64(kind, order, threads, smem, &per_sm);
     if (e) return e;
     if (per_sm < 1) return (int)cudaErrorLaunchOutOfResources;
     int64_t grid = (int64_t)per_sm * sms;
     if (P.total_tiles >= 0 && P.total_tiles < grid) grid = P.total_tiles;
     if (grid < 1) grid = 1;
-    return launch_fwd64(kind, order, P, (int)grid, threads, smem, stream);
+    return mx ? launch_fwdmx(kind, order, P, (int)grid, threads, smem, stream)
+              : launch_fwd64(kind, order, P, (int)grid, threads, smem, stream);
 }
 
 // Prefix sums of tiles per source (one block; each thread scans a contiguous chunk of

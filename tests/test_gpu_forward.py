@@ -15,42 +15,14 @@ if not torch.cuda.is_available():
 import oracle  # noqa: E402
 import paper_2204_06633_gb300 as lr  # noqa: E402
 import synth  # noqa: E402
-from _gpu import Pair, assert_close, dev, host  # noqa: E402
+from _gpu import DT, T0, Pair, assert_close, dev, host, run_case, sky  # noqa: E402
 
-DT, T0 = 10.0, 0.0
 REL64 = 1e-12
 
 
 @pytest.fixture(scope="module")
 def ctx():
     return lr.Context(0)
-
-
-def sky(src):
-    return (src.lam, src.beta, src.psi)
-
-
-def run_case(ctx, src, N, p, porb, torb=None, gen=2, delay_mode=0, kind="response", tile=0):
-    torb = torb or porb
-    t0h, hp, hc = synth.gb_input(src, T0, DT, N, p)
-    plan = lr.Plan(ctx, p, N, DT, porb.gpu, torb.gpu, t0=T0, generation=gen, delay_mode=delay_mode, tile=tile)
-    args = (p, gen, DT, T0, N, porb.orc, torb.orc, hp, hc, t0h, src.lam, src.beta, src.psi)
-    if kind == "response":
-        got = host(plan.response(dev(hp), dev(hc), t0h, sky(src)))
-        ref = oracle.response(*args, delay_mode=delay_mode)
-        scale = oracle.response(*args, delay_mode=delay_mode, absval=True)
-    elif kind == "project":
-        got = host(plan.project(dev(hp), dev(hc), t0h, sky(src)))
-        pargs = (p, DT, T0, N, porb.orc, hp, hc, t0h, src.lam, src.beta, src.psi)
-        ref = oracle.project(*pargs)
-        scale = oracle.project(*pargs, absval=True)
-    else:  # tdi on the oracle's link series
-        y = oracle.project(p, DT, T0, N, porb.orc, hp, hc, t0h, src.lam, src.beta, src.psi)
-        got = host(plan.tdi(dev(y)))
-        ref = oracle.tdi(p, gen, DT, T0, N, torb.orc, y, delay_mode)
-        scale = oracle.tdi(p, gen, DT, T0, N, torb.orc, np.abs(y), delay_mode, absval=True)
-    plan.check()
-    return assert_close(got, ref, scale, p + 1, REL64, f"{kind} p={p} N={N}")
 
 
 def test_config1_plain_method_fp64(ctx):
