@@ -74,6 +74,7 @@ def _load():
             "orc_tdi_adjoint": (I, [I, I, I, D, D, I64, P, dp, dp]),
             "orc_project_adjoint": (I, [I, D, D, I64, P, I64, D, D, D, D, dp, dp, dp]),
             "orc_sky_gradient": (I, [I, D, D, I64, P, dp, dp, I64, D, D, D, D, dp, dp]),
+            "orc_sky_gradient_abs": (I, [I, D, D, I64, P, dp, dp, I64, D, D, D, D, dp, dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -233,17 +234,24 @@ def project_adjoint(p, dt, t0, n, porb: Orbit, nh, t0h, lam, beta, psi, gy):
     return ghp, ghc
 
 
-def sky_gradient(p, dt, t0, n, porb: Orbit, hp, hc, t0h, lam, beta, psi, gy) -> np.ndarray:
+def sky_gradient(p, dt, t0, n, porb: Orbit, hp, hc, t0h, lam, beta, psi, gy, absval: bool = False) -> np.ndarray:
+    """dLoss/d(lambda, beta, psi) given g_y; absval=True returns the rounding-error scale of
+    that sum (every factor by its absolute value), for sizing tolerances."""
     hp, hc, gy = _f64(hp), _f64(hc), _f64(gy)
     g = np.empty(3)
-    _check(_load().orc_sky_gradient(p, dt, t0, n, porb.handle, _dp(hp), _dp(hc), len(hp), t0h, lam, beta, psi,
-                                    _dp(gy), _dp(g)), "sky_gradient")
+    fn = _load().orc_sky_gradient_abs if absval else _load().orc_sky_gradient
+    _check(fn(p, dt, t0, n, porb.handle, _dp(hp), _dp(hc), len(hp), t0h, lam, beta, psi, _dp(gy), _dp(g)),
+           "sky_gradient")
     return g
 
 
-def backward(p, gen, dt, t0, n, porb, torb, hp, hc, t0h, lam, beta, psi, gxyz, delay_mode: int = DELAY_SUM):
-    """Gradient of <gxyz, R(h)> with respect to h+, hx and (lambda, beta, psi)."""
+def backward(p, gen, dt, t0, n, porb, torb, hp, hc, t0h, lam, beta, psi, gxyz, delay_mode: int = DELAY_SUM,
+             with_scale: bool = False):
+    """Gradient of <gxyz, R(h)> with respect to h+, hx and (lambda, beta, psi); with_scale also
+    returns the rounding-error scale of the sky-angle gradient."""
     gy = tdi_adjoint(p, gen, dt, t0, n, torb, gxyz, delay_mode)
     ghp, ghc = project_adjoint(p, dt, t0, n, porb, len(hp), t0h, lam, beta, psi, gy)
     gsky = sky_gradient(p, dt, t0, n, porb, hp, hc, t0h, lam, beta, psi, gy)
+    if with_scale:
+        return ghp, ghc, gsky, sky_gradient(p, dt, t0, n, porb, hp, hc, t0h, lam, beta, psi, gy, absval=True)
     return ghp, ghc, gsky

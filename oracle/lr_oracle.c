@@ -778,3 +778,67 @@ int orc_sky_gradient(int p, double dt, double t0, int64_t N, const void *porb,
     gsky[0] = G[0]; gsky[1] = G[1]; gsky[2] = G[2];
     return 0;
 }
+
+/* Rounding-error scale of the sky-angle gradient: the same sums with every factor replaced by
+ * its absolute value (reads with |w| and |w'|).  Used only to size test tolerances. */
+static double orc_lagrange_dread_abs(const double *s, int64_t ns, int64_t base, double u, int p)
+{
+    double fl = floor(u);
+    int64_t m = base + (int64_t)fl;
+    double eps = u - fl;
+    double dw[ORC_MAX_T];
+    orc_lagrange_dweights(p, eps, dw);
+    int h = (p - 1) / 2;
+    double acc = 0.0;
+    for (int a = 0; a < p + 1; ++a) {
+        int64_t i = m - h + a;
+        if (i >= 0 && i < ns) acc += fabs(dw[a]) * fabs(s[i]);
+    }
+    return acc;
+}
+
+int orc_sky_gradient_abs(int p, double dt, double t0, int64_t N, const void *porb,
+                         const double *hp, const double *hc, int64_t nh, double t0h,
+                         double lam, double beta, double psi, const double *gy, double *gsky)
+{
+    if (p < 1 || (p % 2) == 0 || p + 1 > ORC_MAX_T) return -1;
+    const orc_orbit *po = (const orc_orbit *)porb;
+    orc_sky S;
+    orc_sky_make(lam, beta, psi, &S);
+    double G[3] = {0.0, 0.0, 0.0};
+    for (int64_t n = 0; n < N; ++n) {
+        double t = t0 + (double)n * dt;
+        double x[3][3], L[6];
+        orc_orbit_positions(po, t, x);
+        for (int l = 0; l < 6; ++l) L[l] = orc_orbit_delay(po, l, t);
+        for (int l = 0; l < 6; ++l) {
+            double gl = fabs(gy[(int64_t)l * N + n]);
+            if (gl == 0.0) continue;
+            int r = ORC_LINK_R[l] - 1, s = ORC_LINK_S[l] - 1;
+            orc_link_geo g;
+            orc_link_geometry(l, x, L, &S, t0, dt, t0h, &g);
+            double den = fabs(1.0 / (2.0 * (1.0 - g.kn)));
+            double Ap = orc_lagrange_read_abs(hp, nh, n, g.ue, p) + orc_lagrange_read_abs(hp, nh, n, g.ur, p);
+            double Ac = orc_lagrange_read_abs(hc, nh, n, g.ue, p) + orc_lagrange_read_abs(hc, nh, n, g.ur, p);
+            double dAe_p = orc_lagrange_dread_abs(hp, nh, n, g.ue, p), dAr_p = orc_lagrange_dread_abs(hp, nh, n, g.ur, p);
+            double dAe_c = orc_lagrange_dread_abs(hc, nh, n, g.ue, p), dAr_c = orc_lagrange_dread_abs(hc, nh, n, g.ur, p);
+            double dH = fabs(g.xp) * Ap + fabs(g.xc) * Ac;
+            double a = dot3(S.u, g.n), b = dot3(S.v, g.n);
+            for (int th = 0; th < 2; ++th) {
+                const double *dk = th == 0 ? S.dk_dl : S.dk_db;
+                const double *du = th == 0 ? S.du_dl : S.du_db;
+                const double *dv = th == 0 ? S.dv_dl : S.dv_db;
+                double da = fabs(dot3(du, g.n)), db = fabs(dot3(dv, g.n));
+                double dxi = 2.0 * (fabs(a) * da + fabs(b) * db);
+                double dden = 2.0 * den * den * fabs(dot3(dk, g.n));
+                double due = fabs(dot3(dk, x[s])) / ORC_C / dt, dur = fabs(dot3(dk, x[r])) / ORC_C / dt;
+                double ddH = dxi * (Ap + Ac) + fabs(g.xp) * (dAe_p * due + dAr_p * dur) +
+                             fabs(g.xc) * (dAe_c * due + dAr_c * dur);
+                G[th] += gl * (dden * dH + den * ddH);
+            }
+            G[2] += gl * den * 2.0 * (fabs(g.xc) * Ap + fabs(g.xp) * Ac);
+        }
+    }
+    gsky[0] = G[0]; gsky[1] = G[1]; gsky[2] = G[2];
+    return 0;
+}

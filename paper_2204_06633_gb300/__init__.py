@@ -273,3 +273,29 @@ class Plan:
 
 def order_supported(order: int) -> bool:
     return bool(library().lr_order_supported(int(order)))
+
+
+class _Response(torch.autograd.Function):
+    """X, Y, Z = R(h+, hx; lambda, beta, psi) with the library's adjoint as backward."""
+
+    @staticmethod
+    def forward(ctx, hp, hc, sky, plan, t0h):
+        s = tuple(float(v) for v in sky.detach().cpu().tolist())
+        ctx.plan, ctx.t0h, ctx.sky = plan, t0h, s
+        ctx.save_for_backward(hp, hc)
+        return plan.response(hp.contiguous(), hc.contiguous(), t0h, s)
+
+    @staticmethod
+    def backward(ctx, g_xyz):
+        hp, hc = ctx.saved_tensors
+        g_hp, g_hc, g_sky = ctx.plan.backward(hp.contiguous(), hc.contiguous(), ctx.t0h, ctx.sky,
+                                              g_xyz.contiguous())
+        return g_hp, g_hc, g_sky.to(g_xyz.device), None, None
+
+
+def response(plan: Plan, hp, hc, sky, t0h: float):
+    """Differentiable fused response: gradients flow to h+, hx and sky = (lambda, beta, psi)
+    (a float64 tensor of 3 values)."""
+    if not isinstance(sky, torch.Tensor):
+        sky = torch.tensor(sky, dtype=torch.float64, device=hp.device)
+    return _Response.apply(hp, hc, sky, plan, t0h)

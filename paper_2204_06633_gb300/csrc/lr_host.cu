@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "lr_internal.h"
+#include "lr_bwd.h"
 #include "lr_launch.h"
 
 struct lr_ctx {
@@ -28,6 +29,7 @@ struct lr_orbit {
     double *d_coef;
     double max_r_over_c;          // max_t max_i |x_i(t)| / c  (s)
     double max_delay;             // max_t max_l L_l(t)     (s)
+    double max_rate;              // bound of |d(k.x_i/c)/dt| + |dL_l/dt| (s/s)
 };
 
 struct lr_plan {
@@ -39,6 +41,13 @@ struct lr_plan {
     int *d_err;
     int64_t *d_tile_off;
     int64_t tile_cap;
+    // backward workspace: link-series gradient, per-tile sky partials, batch tile tables
+    double *d_gy;
+    int64_t gy_cap;
+    double *d_partial;
+    int64_t partial_cap;
+    int64_t *d_ktile_off, *d_htile_off;
+    int64_t ktile_cap;
 };
 
 namespace {
@@ -306,10 +315,17 @@ LR_API int lr_orbit_create(lr_ctx *ctx, const double *t_knots, int64_t n_knots, 
     }
     // bounds over the grid, sampled on knots and at 8 points per interval (the cubic pieces
     // of smooth orbits overshoot their knot values only by a tiny amount)
-    double rmax = 0.0, lmax = 0.0;
+    double rmax = 0.0, lmax = 0.0, vmax = 0.0, ldot = 0.0;
     for (int k = 0; k < o->nint; ++k)
         for (int j = 0; j <= 8; ++j) {
             double t = o->t_first + ((double)k + j / 8.0) * dk;
+            // derivative of each cubic piece: (b + 2 c x + 3 d x^2) / dk
+            const double x = j / 8.0;
+            for (int s = 0; s < lr::NSERIES; ++s) {
+                const double *q = o->coef.data() + ((size_t)k * lr::NSERIES + s) * 4;
+                double dv = std::fabs((q[1] + x * (2.0 * q[2] + 3.0 * x * q[3])) / dk);
+                if (s < 9) vmax = std::max(vmax, dv); else ldot = std::max(ldot, dv);
+            }
             for (int i = 0; i < 3; ++i) {
                 double r2 = 0.0;
                 for (int d = 0; d < 3; ++d) {
@@ -322,6 +338,12 @@ LR_API int lr_orbit_create(lr_ctx *ctx, const double *t_knots, int64_t n_knots, 
         }
     o->max_r_over_c = rmax / lr::C_LIGHT * (1.0 + 1e-3) + 1e-3;
     o->max_delay = lmax * (1.0 + 1e-3) + 1e-3;
+    o->max_rate = (std::sqrt(3.0) * vmax / lr::C_LIGHT + ldot) * 1.1 + 1e-9;
+    for (size_t i = 0; i < o->delays.size(); ++i)
+        if (!(o->delays[i] > 0.0)) {
+            delete o;
+            return LR_ERR_RANGE;  // light travel times are positive
+        }
     cudaError_t e = cudaMalloc(&o->d_coef, sizeof(double) * o->coef.size());
     if (e != cudaSuccess) {
         delete o;
@@ -380,6 +402,12 @@ LR_API int lr_plan_create(lr_ctx *ctx, const lr_plan_desc *d, lr_plan **out)
     p->d_err = nullptr;
     p->d_tile_off = nullptr;
     p->tile_cap = 0;
+    p->d_gy = nullptr;
+    p->gy_cap = 0;
+    p->d_partial = nullptr;
+    p->partial_cap = 0;
+    p->d_ktile_off = p->d_htile_off = nullptr;
+    p->ktile_cap = 0;
     lr::FwdParams &P = p->base;
     std::memset(&P, 0, sizeof(P));
     P.dt = d->dt;
@@ -444,6 +472,10 @@ LR_API int lr_plan_destroy(lr_plan *plan)
     if (!plan) return LR_ERR_INVALID_ARG;
     if (plan->d_err) cudaFree(plan->d_err);
     if (plan->d_tile_off) cudaFree(plan->d_tile_off);
+    if (plan->d_gy) cudaFree(plan->d_gy);
+    if (plan->d_partial) cudaFree(plan->d_partial);
+    if (plan->d_ktile_off) cudaFree(plan->d_ktile_off);
+    if (plan->d_htile_off) cudaFree(plan->d_htile_off);
     delete plan;
     return LR_OK;
 }
@@ -474,6 +506,58 @@ LR_API int lr_plan_check(lr_plan *plan, void *stream)
 }
 
 }  // extern "C"
+
+namespace {
+
+// Sizes the backward launch parameters and grows the plan's workspace.
+int backward_setup(lr_plan *plan, int64_t gy_elems, int64_t ktiles, lr::FwdParams &P, lr::BwdParams &B)
+{
+    P = plan->base;
+    std::memset(&B, 0, sizeof(B));
+    P.tile = lr::BWD_TILE_K;
+    P.wmax = lr::BWD_TILE_K + 2 * P.sig_b + P.lproj_b + plan->T + 4;
+    const double chain = (double)P.q_terms * plan->desc.tdi_orbit->max_delay / plan->desc.dt;
+    B.dmax = (int)std::ceil(chain) + 1;
+    B.tile_h = lr::BWD_TILE_H;
+    B.wn = lr::BWD_TILE_K + 2 * plan->h + 5 + B.dmax;
+    const double span = (double)(lr::BWD_TILE_H + plan->T + 2 * (P.sig_b + P.lproj_b));
+    B.kmargin = 2 + (int)std::ceil(plan->desc.proj_orbit->max_rate * span);
+    B.wk = lr::BWD_TILE_H + plan->T + 5 + 2 * P.lproj_b + 2 * B.kmargin;
+    if (gy_elems > plan->gy_cap) {
+        if (plan->d_gy) cudaFree(plan->d_gy);
+        plan->d_gy = nullptr;
+        plan->gy_cap = 0;
+        cudaError_t e = cudaMalloc(&plan->d_gy, sizeof(double) * (size_t)gy_elems);
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LR_ERR_OOM : cuda_fail(plan->ctx, e);
+        plan->gy_cap = gy_elems;
+    }
+    if (3 * ktiles > plan->partial_cap) {
+        if (plan->d_partial) cudaFree(plan->d_partial);
+        plan->d_partial = nullptr;
+        plan->partial_cap = 0;
+        cudaError_t e = cudaMalloc(&plan->d_partial, sizeof(double) * (size_t)(3 * ktiles));
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LR_ERR_OOM : cuda_fail(plan->ctx, e);
+        plan->partial_cap = 3 * ktiles;
+    }
+    B.g_y = plan->d_gy;
+    B.partial = plan->d_partial;
+    return LR_OK;
+}
+
+// TDI transpose, sky partials, projection transpose, then the ordered sky reduction.
+int backward_launch(lr_plan *plan, lr::FwdParams &P, lr::BwdParams &B, int64_t S, const int64_t *ktile_off,
+                    double *g_sky, void *stream)
+{
+    const int sms = plan->ctx->sms;
+    const int order = plan->desc.order;
+    int e = lr::launch_bwd(0, order, P, B, sms, stream);
+    if (!e && g_sky) e = lr::launch_bwd(2, order, P, B, sms, stream);
+    if (!e) e = lr::launch_bwd(1, order, P, B, sms, stream);
+    if (!e && g_sky) e = lr::launch_sky_reduce(B.partial, ktile_off, S, P.total_tiles, g_sky, stream);
+    return check_launch(plan->ctx, e);
+}
+
+}  // namespace
 
 // ================================================================== launches
 namespace {
@@ -574,18 +658,82 @@ LR_API int lr_response_batched(lr_plan *plan, int64_t S, const int64_t *h_off, c
 LR_API int lr_backward(lr_plan *plan, const double *hp, const double *hc, int64_t n_h, double t0_h, lr_sky sky,
                        const double *g_xyz, double *g_hp, double *g_hc, double *g_sky, void *stream)
 {
-    (void)plan; (void)hp; (void)hc; (void)n_h; (void)t0_h; (void)sky; (void)g_xyz; (void)g_hp; (void)g_hc;
-    (void)g_sky; (void)stream;
-    return LR_ERR_UNSUPPORTED;
+    if (!plan || !hp || !hc || !g_xyz || !g_hp || !g_hc) return LR_ERR_INVALID_ARG;
+    if (n_h < 1) return LR_ERR_INVALID_ARG;
+    if (!std::isfinite(t0_h) || !std::isfinite(sky.lam) || !std::isfinite(sky.beta) || !std::isfinite(sky.psi))
+        return LR_ERR_NONFINITE;
+    if (std::fabs(plan->desc.t0 - t0_h) / plan->desc.dt > 1e12) return LR_ERR_RANGE;
+    lr::FwdParams P;
+    lr::BwdParams B;
+    const int64_t N = plan->desc.n;
+    const int64_t ktiles = (N + lr::BWD_TILE_K - 1) / lr::BWD_TILE_K;
+    int st = backward_setup(plan, 6 * N, ktiles, P, B);
+    if (st) return st;
+    P.src.n1 = N;
+    P.src.nh1 = n_h;
+    P.src.t0h1 = t0_h;
+    P.src.sky1 = sky;
+    P.hp = hp;
+    P.hc = hc;
+    P.out = const_cast<double *>(g_xyz);  // base of the per-source output offsets
+    P.total_tiles = ktiles;
+    B.g_xyz = g_xyz;
+    B.g_hp = g_hp;
+    B.g_hc = g_hc;
+    B.h_tile_off = nullptr;
+    B.h_total_tiles = (n_h + lr::BWD_TILE_H - 1) / lr::BWD_TILE_H;
+    return backward_launch(plan, P, B, 1, nullptr, g_sky, stream);
 }
 
 LR_API int lr_backward_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
                                const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
                                const double *g_xyz, double *g_hp, double *g_hc, double *g_sky, void *stream)
 {
-    (void)plan; (void)S; (void)h_off; (void)out_off; (void)t0_h; (void)sky; (void)hp; (void)hc; (void)g_xyz;
-    (void)g_hp; (void)g_hc; (void)g_sky; (void)stream;
-    return LR_ERR_UNSUPPORTED;
+    if (!plan || !h_off || !out_off || !t0_h || !sky || !hp || !hc || !g_xyz || !g_hp || !g_hc)
+        return LR_ERR_INVALID_ARG;
+    if (S < 1) return LR_ERR_INVALID_ARG;
+    if (S > (int64_t)1 << 24) return LR_ERR_RANGE;
+    // the workspace is sized from the total output length: one small device-to-host read
+    int64_t total_n = 0;
+    cudaError_t e = cudaMemcpyAsync(&total_n, out_off + S, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                    (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(plan->ctx, e);
+    if (total_n < 0) return LR_ERR_INVALID_ARG;
+    const int64_t ktiles_bound = total_n / lr::BWD_TILE_K + S + 1;
+    lr::FwdParams P;
+    lr::BwdParams B;
+    int st = backward_setup(plan, 6 * (total_n > 0 ? total_n : 1), ktiles_bound, P, B);
+    if (st) return st;
+    if (S + 1 > plan->ktile_cap) {
+        if (plan->d_ktile_off) cudaFree(plan->d_ktile_off);
+        if (plan->d_htile_off) cudaFree(plan->d_htile_off);
+        plan->d_ktile_off = plan->d_htile_off = nullptr;
+        plan->ktile_cap = 0;
+        e = cudaMalloc(&plan->d_ktile_off, sizeof(int64_t) * (size_t)(S + 1));
+        if (e == cudaSuccess) e = cudaMalloc(&plan->d_htile_off, sizeof(int64_t) * (size_t)(S + 1));
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LR_ERR_OOM : cuda_fail(plan->ctx, e);
+        plan->ktile_cap = S + 1;
+    }
+    int le = lr::launch_tile_offsets(out_off, S, lr::BWD_TILE_K, plan->d_ktile_off, P.err, stream);
+    if (!le) le = lr::launch_tile_offsets(h_off, S, lr::BWD_TILE_H, plan->d_htile_off, P.err, stream);
+    if (le) return check_launch(plan->ctx, le);
+    P.src.h_off = h_off;
+    P.src.out_off = out_off;
+    P.src.t0h = t0_h;
+    P.src.sky = sky;
+    P.src.tile_off = plan->d_ktile_off;
+    P.src.S = S;
+    P.hp = hp;
+    P.hc = hc;
+    P.out = const_cast<double *>(g_xyz);
+    P.total_tiles = -1;
+    B.g_xyz = g_xyz;
+    B.g_hp = g_hp;
+    B.g_hc = g_hc;
+    B.h_tile_off = plan->d_htile_off;
+    B.h_total_tiles = -1;
+    return backward_launch(plan, P, B, S, plan->d_ktile_off, g_sky, stream);
 }
 
 }  // extern "C"
