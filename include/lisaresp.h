@@ -165,6 +165,24 @@ LR_API int lr_backward(lr_plan *plan, const double *hp, const double *hc, int64_
 LR_API int lr_response_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
                                const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
                                double *xyz, void *stream);
+/* Batched forward that allocates no device memory.  Same arguments, results and asynchrony as
+ * lr_response_batched, which allocates its per-batch tile table on first use; this variant keeps
+ * that table in a fixed device array inside the library, for callers that may not allocate device
+ * memory once their run has started (a sampler or service that has budgeted all device memory
+ * up front, or that cannot take the device-wide synchronisation of cudaMalloc / cudaFree).
+ * The paper has no counterpart: it is an allocation policy of this library.
+ *   S <= LR_NOALLOC_MAX_SOURCES, else LR_ERR_RANGE (nothing is launched).
+ *   The array (8 * (LR_NOALLOC_MAX_SOURCES + 1) bytes) is held by every GPU that loads the
+ *   library until the process exits, and is shared by every call on that GPU: each call rewrites
+ *   the entries it uses before reading them, and calls that overlap on the GPU (other streams,
+ *   other threads, other plans) race on it.  The first call on a device looks up the array's
+ *   device address (cudaGetSymbolAddress, with that device made current for the look-up); make
+ *   that first call before any stream capture. */
+#define LR_NOALLOC_MAX_SOURCES 65536
+LR_API int lr_response_batched_noalloc(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
+                                       const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
+                                       double *xyz, void *stream);
+
 /* Batched transpose; g_sky is DEVICE [S][3] (may be NULL). */
 LR_API int lr_backward_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
                                const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,

@@ -64,7 +64,9 @@ _SIGS = {
     "lr_backward": (_I, [_P, _P, _P, _I64, _D, lr_sky, _P, _P, _P, _P, _P]),
     "lr_response_batched": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
     "lr_backward_batched": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "lr_response_batched_noalloc": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
 }
+NOALLOC_MAX_SOURCES = 65536
 
 
 def library() -> ctypes.CDLL:
@@ -252,6 +254,17 @@ class Plan:
         total = int(out_off[-1].item()) if xyz is None else xyz.numel() // 3
         xyz = self._out(xyz, (3 * total,), hp)
         _check("lr_response_batched", library().lr_response_batched(
+            self._h, S, _devi64(h_off, "h_off", S + 1), _devi64(out_off, "out_off", S + 1), _dev64(t0h, "t0h", S),
+            _dev64(sky, "sky", 3 * S), _dev64(hp, "hp"), _dev64(hc, "hc", hp.numel()), _dev64(xyz, "xyz"),
+            _stream_handle(stream)))
+        return xyz
+
+    def response_batched_noalloc(self, h_off, out_off, t0h, sky, hp, hc, xyz, stream=None):
+        """lr_response_batched without any device allocation inside the call (the tile table
+        lives in a fixed device array, S <= NOALLOC_MAX_SOURCES); `xyz` must be preallocated.
+        Calls that overlap on the GPU share that array and race."""
+        S = t0h.numel()
+        _check("lr_response_batched_noalloc", library().lr_response_batched_noalloc(
             self._h, S, _devi64(h_off, "h_off", S + 1), _devi64(out_off, "out_off", S + 1), _dev64(t0h, "t0h", S),
             _dev64(sky, "sky", 3 * S), _dev64(hp, "hp"), _dev64(hc, "hc", hp.numel()), _dev64(xyz, "xyz"),
             _stream_handle(stream)))

@@ -12,6 +12,7 @@
 #include "lr_internal.h"
 #include "lr_bwd.h"
 #include "lr_launch.h"
+#include "lr_planview.h"
 
 struct lr_ctx {
     int device;
@@ -737,3 +738,22 @@ LR_API int lr_backward_batched(lr_plan *plan, int64_t S, const int64_t *h_off, c
 }
 
 }  // extern "C"
+
+// ================================================================== plan view
+namespace lr {
+
+int plan_view(const lr_plan *plan, PlanView *v)
+{
+    if (!plan || !v) return LR_ERR_INVALID_ARG;
+    v->base = plan->base;
+    v->precision = plan->desc.precision;
+    v->order = plan->desc.order;
+    v->threads = plan->threads;
+    v->sms = plan->ctx->sms;
+    v->device = plan->ctx->device;
+    return LR_OK;
+}
+
+int plan_cuda_fail(lr_plan *plan, int cuda_error) { return cuda_fail(plan ? plan->ctx : nullptr, (cudaError_t)cuda_error); }
+
+}  // namespace lr

@@ -1,0 +1,88 @@
+// Batched forward response that allocates no device memory.
+//
+// lr_response_batched keeps its per-batch tile table in memory the plan allocates with
+// cudaMalloc on first use (and re-allocates when a larger batch arrives).  Some callers may
+// not allocate at that point: a sampler or serving process that has handed its whole device
+// memory budget to its own allocator up front, or one that cannot afford the device-wide
+// synchronisation a cudaMalloc / cudaFree implies in the middle of a run.  This variant keeps
+// the tile table in a fixed file-scope device array instead, so the call itself allocates
+// nothing; the price is a fixed capacity (LR_NOALLOC_MAX_SOURCES sources) held by every GPU
+// that loads the library, for the life of the process.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "lr_launch.h"
+#include "lr_planview.h"
+
+namespace {
+
+constexpr int64_t kMaxSources = LR_NOALLOC_MAX_SOURCES;
+constexpr int kMaxDevices = 64;
+
+// the tile table: prefix sums of tiles per source, [S+1] entries, rewritten in full by every call
+static __device__ __align__(256) int64_t g_tile_table[kMaxSources + 1];
+
+// device address of g_tile_table on each device, looked up once per device
+int64_t *g_table_addr[kMaxDevices];
+std::mutex g_table_mutex;
+
+// In host code g_tile_table names a host-side stand-in, not device memory: its device address
+// comes from cudaGetSymbolAddress, taken once per device with that device current.
+int table_address(int device, int64_t **out)
+{
+    if (device < 0 || device >= kMaxDevices) return (int)cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_table_mutex);
+    if (!g_table_addr[device]) {
+        int prev = -1;
+        cudaError_t e = cudaGetDevice(&prev);
+        if (e != cudaSuccess) return (int)e;
+        if (prev != device) {
+            e = cudaSetDevice(device);
+            if (e != cudaSuccess) return (int)e;
+        }
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_tile_table);
+        if (prev != device) {
+            cudaError_t e2 = cudaSetDevice(prev);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e != cudaSuccess) return (int)e;
+        g_table_addr[device] = static_cast<int64_t *>(p);
+    }
+    *out = g_table_addr[device];
+    return 0;
+}
+
+}  // namespace
+
+extern "C" LR_API int lr_response_batched_noalloc(lr_plan *plan, int64_t S, const int64_t *h_off,
+                                                  const int64_t *out_off, const double *t0_h, const lr_sky *sky,
+                                                  const double *hp, const double *hc, double *xyz, void *stream)
+{
+    if (!plan || !h_off || !out_off || !t0_h || !sky || !hp || !hc || !xyz) return LR_ERR_INVALID_ARG;
+    if (S < 1) return LR_ERR_INVALID_ARG;
+    if (S > kMaxSources) return LR_ERR_RANGE;
+    lr::PlanView v;
+    int st = lr::plan_view(plan, &v);
+    if (st) return st;
+    int64_t *table = nullptr;
+    int e = table_address(v.device, &table);
+    if (e) return lr::plan_cuda_fail(plan, e);
+    lr::FwdParams P = v.base;
+    // every entry of the table the launch reads ([0, S]) is written first by this kernel
+    e = lr::launch_tile_offsets(out_off, S, P.tile, table, P.err, stream);
+    if (e) return lr::plan_cuda_fail(plan, e);
+    P.src.h_off = h_off;
+    P.src.out_off = out_off;
+    P.src.t0h = t0_h;
+    P.src.sky = sky;
+    P.src.tile_off = table;
+    P.src.S = S;
+    P.hp = hp;
+    P.hc = hc;
+    P.out = xyz;
+    P.total_tiles = -1;
+    e = lr::launch_forward(v.precision, lr::KIND_FUSED, v.order, P, v.threads, v.sms, stream);
+    return e ? lr::plan_cuda_fail(plan, e) : LR_OK;
+}
