@@ -37,6 +37,8 @@ DT, T0, ORDER, S_SOURCES = 10.0, 0.0, 25, 1024
 # weight vectors x ~3 T flops, ~500 flops of orbit splines and geometry
 FLOPS_PER_SAMPLE = lambda p: 273 * (p + 1) + 500  # noqa: E731
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (nominal; our DFMA probe measured 1.20)
+# FP32 ALU peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def workload(rank: int, n_sources: int):
@@ -124,6 +126,24 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_scalar(value: float, op: str, device=None) -> float:
+    """max or sum of a per-rank scalar over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_throughput(samples_local: int, ms_local: float, device=None):
+    """Whole-job link-samples/s: every rank processes its own batch (weak scaling), so the job
+    moved 6 * (sum of all ranks' samples) in the slowest rank's time."""
+    total = reduce_scalar(samples_local, "sum", device)
+    ms = reduce_scalar(ms_local, "max", device)
+    return 6.0 * total / (ms * 1e-3), ms, total
+
+
 def oracle_rate(lens, srcs, p, orb, budget_s=12.0, sources=4):
     """The FP64 oracle (as it stands) on a bounded sample of the workload: the first `sources`
     sources, each truncated to a prefix sized so the whole sample takes about budget_s."""
@@ -131,7 +151,7 @@ def oracle_rate(lens, srcs, p, orb, budget_s=12.0, sources=4):
     cores = oracle.set_threads(os.cpu_count() or 1)
     o = oracle.Orbit(orb.t_knots, orb.pos, None)
     # calibrate on a short prefix
-    n_try = 2000
+    n_try = 20000
     src = srcs[0]
     t0h, hp, hc = synth.gb_input(src, T0, DT, n_try, p)
     t = time.perf_counter()
@@ -193,8 +213,6 @@ def run_ours(args):
 
     ctx = lr.Context(local)
     o = lr.Orbit(ctx, orb.t_knots, orb.pos, None)
-    precision = lr.MIXED if args.precision == "mixed" else lr.FP64
-    plan = lr.Plan(ctx, p, 1, DT, o, t0=T0, precision=precision, tile=args.tile)
     d_hoff = torch.tensor(h_off, device=dev)
     d_ooff = torch.tensor(out_off, device=dev)
     d_t0h = torch.tensor(t0h, device=dev)
@@ -204,41 +222,50 @@ def run_ours(args):
     d_xyz = torch.empty(3 * total_samples, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step():
-        plan.response_batched(d_hoff, d_ooff, d_t0h, d_sky, d_hp, d_hc, d_xyz, stream=stream)
-
     def barrier():
         if ws > 1:
             import torch.distributed as dist
             dist.barrier()
 
-    for _ in range(args.warmup):
-        step()
-    plan.check(stream)
-    barrier()
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    with ClockSampler(local) as clk:
+    def max_over_ranks(v: float) -> float:
+        return reduce_scalar(v, "max", dev)
+
+    def timed(plan, steps, warmup, sample_clocks=False):
+        """W untimed steps, then K steps bracketed by barrier + synchronize; returns
+        (ms per step, max over ranks; per-launch ms of this rank; clock summary)."""
+        def step():
+            plan.response_batched(d_hoff, d_ooff, d_t0h, d_sky, d_hp, d_hc, d_xyz, stream=stream)
+
+        for _ in range(warmup):
+            step()
+        plan.check(stream)
+        barrier()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        clk = ClockSampler(local) if sample_clocks else None
+        if clk:
+            clk.__enter__()
         t_start = torch.cuda.Event(enable_timing=True)
         t_end = torch.cuda.Event(enable_timing=True)
         t_start.record(stream)
-        for i in range(args.steps):
+        for i in range(steps):
             ev[i][0].record(stream)
             step()
             ev[i][1].record(stream)
         t_end.record(stream)
         torch.cuda.synchronize()
-    barrier()
-    plan.check(stream)
-    ms_total = t_start.elapsed_time(t_end)
-    launch_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.all_reduce(ms, op=dist.ReduceOp.MAX)
-    ms_step = float(ms.item()) / args.steps
-    link_samples = 6.0 * total_samples * ws
-    value = link_samples / (ms_step * 1e-3)
+        if clk:
+            clk.__exit__(None, None, None)
+        barrier()
+        plan.check(stream)
+        ms = max_over_ranks(t_start.elapsed_time(t_end)) / steps
+        return ms, [a.elapsed_time(b) for a, b in ev], (clk.summary() if clk else None), step
+
+    precision = lr.MIXED if args.precision == "mixed" else lr.FP64
+    plan = lr.Plan(ctx, p, 1, DT, o, t0=T0, precision=precision, tile=args.tile)
+    ms_step, launch_ms, clocks, step = timed(plan, args.steps, args.warmup, sample_clocks=True)
+    value, ms_step, job_samples = job_throughput(total_samples, ms_step, dev)
+    link_samples = 6.0 * job_samples
 
     # accuracy at the stated precision: sampled outputs of a few sources against the oracle
     rel_err = None
@@ -268,22 +295,39 @@ def run_ours(args):
             e2e_step()
         b.record(stream)
         torch.cuda.synchronize()
-        t = torch.tensor([a.elapsed_time(b) / n_e2e], dtype=torch.float64, device=dev)
-        if ws > 1:
-            import torch.distributed as dist
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = {"value": link_samples / (float(t.item()) * 1e-3), "unit": "link-samples/s",
+        t = max_over_ranks(a.elapsed_time(b) / n_e2e)
+        e2e = {"value": link_samples / (t * 1e-3), "unit": "link-samples/s",
                "h2d_bytes_per_step": int(hp.nbytes + hc.nbytes), "d2h_bytes_per_step": int(out_pin.numel() * 8)}
+
+    # the same batch in plain FP64 on the same GPU (the comparison the metric names)
+    fp64 = None
+    if precision == lr.MIXED and not args.no_fp64:
+        plan64 = lr.Plan(ctx, p, 1, DT, o, t0=T0, precision=lr.FP64)
+        ms64, l64, _, _ = timed(plan64, 2, 1)
+        fp64 = {"value": link_samples / (ms64 * 1e-3), "unit": "link-samples/s", "ms_per_step": ms64,
+                "steps": 2, "warmup": 1, "mixed_speedup": ms64 / ms_step,
+                "roofline": {"bound": "alu", "achieved": FLOPS_PER_SAMPLE(p) * total_samples /
+                             (statistics.mean(l64) * 1e-3) / 1e12, "peak": FP64_NOMINAL_TFLOPS,
+                             "unit": "TFLOP/s", "frac": FLOPS_PER_SAMPLE(p) * total_samples /
+                             (statistics.mean(l64) * 1e-3) / 1e12 / FP64_NOMINAL_TFLOPS}}
+        if rank == 0 and not args.no_check:
+            fp64["rel_error_vs_oracle"] = sampled_error(d_xyz, lens, srcs, out_off, orb, p)
 
     if rank != 0:
         return
     avg_launch_s = statistics.mean(launch_ms) * 1e-3
     flops = FLOPS_PER_SAMPLE(p) * total_samples
-    peak_tflops = FP64_NOMINAL_TFLOPS
+    if precision == lr.FP64:
+        peak_tflops, src_peak = FP64_NOMINAL_TFLOPS, "GB300 FP64 nominal 1.25 TFLOP/s (own DFMA probe: 1.20)"
+    else:
+        peak_tflops, src_peak = FP32_PEAK_TFLOPS, ("FP32 ALU peak 152 SM x 128 lanes x 2 flop x 2.07 GHz "
+                                                   "(own FFMA probe: 74.9 TFLOP/s)")
     roof = {"bound": "alu", "achieved": flops / avg_launch_s / 1e12, "peak": peak_tflops, "unit": "TFLOP/s",
-            "frac": flops / avg_launch_s / 1e12 / peak_tflops, "traffic": None,
-            "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (own DFMA probe: 1.20)",
-            "algorithmic_flops_per_sample": FLOPS_PER_SAMPLE(p)}
+            "frac": flops / avg_launch_s / 1e12 / peak_tflops, "traffic": None, "peak_source": src_peak,
+            "algorithmic_flops_per_sample": FLOPS_PER_SAMPLE(p),
+            "kernel": "k_mixed<T,FUSED>" if precision == lr.MIXED else "k_fused64<T>",
+            "timing": "CUDA events around each batched call on its stream (tile-table kernel + fused kernel; "
+                      "the fused kernel is 99.9 % of it by the ncu launch list)"}
     line = {"metric": METRIC, "value": value, "unit": "link-samples/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if precision == lr.FP64 else "f32 taps + f64 index",
@@ -295,7 +339,7 @@ def run_ours(args):
                        "samples_per_gpu": total_samples, "l2": "inputs (%.1f GB) larger than L2" %
                        ((hp.nbytes + hc.nbytes) / 1e9), "tile": plan.desc.tile},
             "rel_error_vs_oracle": rel_err, "roofline": roof, "e2e": e2e, "gpu_launches": 2 * args.steps,
-            "clocks": clk.summary()}
+            "clocks": clocks, "fp64": fp64}
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = oracle_rate(lens, srcs, p, orb)
     print(json.dumps(line), flush=True)
@@ -324,7 +368,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison run")
     ap.add_argument("--order", type=int, default=ORDER)
     ap.add_argument("--sources", type=int, default=S_SOURCES)
     ap.add_argument("--tile", type=int, default=0)
