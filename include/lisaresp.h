@@ -95,6 +95,9 @@ typedef struct {
 LR_API const char *lr_strerror(int status);
 LR_API int lr_version(void);                        /* major*10000 + minor*100 + patch */
 LR_API int lr_order_supported(int order);           /* 1 if a kernel for this degree is compiled */
+/* Failure injection for tests: after `after` more successful device allocations, every further
+ * library allocation fails with LR_ERR_OOM (after < 0 disables; process-wide, not thread-safe). */
+LR_API int lr_debug_fail_allocations(int after);
 
 /* ------------------------------------------------------------------ context */
 /* Binds the library to CUDA device `device` (>= 0).  *out is owned by the caller and freed
@@ -165,6 +168,24 @@ LR_API int lr_backward(lr_plan *plan, const double *hp, const double *hc, int64_
 LR_API int lr_response_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
                                const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
                                double *xyz, void *stream);
+/* ------------------------------------------------------------------ graphs and tuning */
+typedef struct lr_graph lr_graph;
+/* Captures one lr_response_batched call (tile-table kernel + persistent fused kernel) into an
+ * instantiated CUDA graph.  The plan's batch workspace is reserved before the capture; the graph
+ * keeps the given device pointers: rewrite the inputs in place between replays.  The batch
+ * shape (S, offsets) must not change while the graph is used.  Owned by the caller. */
+LR_API int lr_response_batched_graph(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
+                                     const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
+                                     double *xyz, lr_graph **out);
+LR_API int lr_graph_launch(lr_graph *graph, void *stream);  /* replay on `stream` */
+LR_API int lr_graph_destroy(lr_graph *graph);
+/* Times the fused forward on a synthetic single source of n_samples outputs for a few candidate
+ * tile sizes and keeps the fastest in the plan (*tile_out).  With use_cache the choice is read
+ * from / appended to a text cache (path from LR_AUTOTUNE_CACHE, default
+ * $HOME/.cache/lisaresp_autotune.txt) keyed by GPU name, precision, order, TDI generation and
+ * log2 length bucket.  Allocates and frees temporary device buffers; synchronizes `stream`. */
+LR_API int lr_plan_autotune(lr_plan *plan, int64_t n_samples, int use_cache, void *stream, int *tile_out);
+
 /* Batched forward that allocates no device memory.  Same arguments, results and asynchrony as
  * lr_response_batched, which allocates its per-batch tile table on first use; this variant keeps
  * that table in a fixed device array inside the library, for callers that may not allocate device

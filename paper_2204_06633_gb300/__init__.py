@@ -48,6 +48,7 @@ _SIGS = {
     "lr_strerror": (ctypes.c_char_p, [_I]),
     "lr_version": (_I, []),
     "lr_order_supported": (_I, [_I]),
+    "lr_debug_fail_allocations": (_I, [_I]),
     "lr_ctx_create": (_I, [_I, _PP]),
     "lr_ctx_destroy": (_I, [_P]),
     "lr_last_cuda_error": (_I, [_P]),
@@ -65,6 +66,10 @@ _SIGS = {
     "lr_response_batched": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
     "lr_backward_batched": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "lr_response_batched_noalloc": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "lr_response_batched_graph": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _PP]),
+    "lr_graph_launch": (_I, [_P, _P]),
+    "lr_graph_destroy": (_I, [_P]),
+    "lr_plan_autotune": (_I, [_P, _I64, _I, _P, ctypes.POINTER(_I)]),
 }
 NOALLOC_MAX_SOURCES = 65536
 
@@ -259,6 +264,24 @@ class Plan:
             _stream_handle(stream)))
         return xyz
 
+    def autotune(self, n_samples: int, use_cache: bool = True, stream=None) -> int:
+        """Time candidate tile sizes on a synthetic series and keep the fastest; returns it."""
+        t = ctypes.c_int(0)
+        _check("lr_plan_autotune", library().lr_plan_autotune(self._h, int(n_samples), 1 if use_cache else 0,
+                                                              _stream_handle(stream), ctypes.byref(t)))
+        self.desc.tile = t.value
+        return t.value
+
+    def response_batched_graph(self, h_off, out_off, t0h, sky, hp, hc, xyz):
+        """Capture the batched call into a replayable CUDA graph (fixed pointers)."""
+        S = t0h.numel()
+        h = ctypes.c_void_p()
+        _check("lr_response_batched_graph", library().lr_response_batched_graph(
+            self._h, S, _devi64(h_off, "h_off", S + 1), _devi64(out_off, "out_off", S + 1), _dev64(t0h, "t0h", S),
+            _dev64(sky, "sky", 3 * S), _dev64(hp, "hp"), _dev64(hc, "hc", hp.numel()), _dev64(xyz, "xyz"),
+            ctypes.byref(h)))
+        return Graph(h, keep=(h_off, out_off, t0h, sky, hp, hc, xyz, self))
+
     def response_batched_noalloc(self, h_off, out_off, t0h, sky, hp, hc, xyz, stream=None):
         """lr_response_batched without any device allocation inside the call (the tile table
         lives in a fixed device array, S <= NOALLOC_MAX_SOURCES); `xyz` must be preallocated.
@@ -286,6 +309,22 @@ class Plan:
 
 def order_supported(order: int) -> bool:
     return bool(library().lr_order_supported(int(order)))
+
+
+class Graph:
+    """An instantiated CUDA graph of one batched response call."""
+
+    def __init__(self, handle, keep):
+        self._h = handle
+        self._keep = keep  # the captured buffers must outlive the graph
+
+    def launch(self, stream=None):
+        _check("lr_graph_launch", library().lr_graph_launch(self._h, _stream_handle(stream)))
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.lr_graph_destroy(self._h)
+            self._h = None
 
 
 class _Response(torch.autograd.Function):

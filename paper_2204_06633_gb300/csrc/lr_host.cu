@@ -51,12 +51,28 @@ struct lr_plan {
     int64_t ktile_cap;
 };
 
+namespace lr {
+// Fault injection for tests: after `g_alloc_budget` more successful allocations every further
+// library allocation fails as if the device were out of memory (negative: disabled).
+static int g_alloc_budget = -1;
+
+cudaError_t dev_malloc(void **p, size_t bytes)
+{
+    if (g_alloc_budget == 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    if (g_alloc_budget > 0) --g_alloc_budget;
+    return cudaMalloc(p, bytes);
+}
+}  // namespace lr
+
 namespace {
 
 int cuda_fail(lr_ctx *ctx, cudaError_t e)
 {
     if (ctx) ctx->last_cuda_error = (int)e;
-    return LR_ERR_CUDA;
+    return e == cudaErrorMemoryAllocation ? LR_ERR_OOM : LR_ERR_CUDA;
 }
 
 int check_launch(lr_ctx *ctx, int e)
@@ -226,6 +242,12 @@ LR_API const char *lr_strerror(int status)
 
 LR_API int lr_version(void) { return 100; }
 
+LR_API int lr_debug_fail_allocations(int after)
+{
+    lr::g_alloc_budget = after < 0 ? -1 : after;
+    return LR_OK;
+}
+
 LR_API int lr_order_supported(int order) { return lr::order_supported(order) ? 1 : 0; }
 
 LR_API int lr_ctx_create(int device, lr_ctx **out)
@@ -345,7 +367,7 @@ LR_API int lr_orbit_create(lr_ctx *ctx, const double *t_knots, int64_t n_knots, 
             delete o;
             return LR_ERR_RANGE;  // light travel times are positive
         }
-    cudaError_t e = cudaMalloc(&o->d_coef, sizeof(double) * o->coef.size());
+    cudaError_t e = lr::dev_malloc((void **)&o->d_coef, sizeof(double) * o->coef.size());
     if (e != cudaSuccess) {
         delete o;
         return e == cudaErrorMemoryAllocation ? LR_ERR_OOM : cuda_fail(ctx, e);
@@ -456,7 +478,7 @@ LR_API int lr_plan_create(lr_ctx *ctx, const lr_plan_desc *d, lr_plan **out)
         }
     }
     chebyshev_inverse(P.cheb);
-    cudaError_t e = cudaMalloc(&p->d_err, sizeof(int));
+    cudaError_t e = lr::dev_malloc((void **)&p->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
     if (e != cudaSuccess) {
         if (p->d_err) cudaFree(p->d_err);
@@ -528,7 +550,7 @@ int backward_setup(lr_plan *plan, int64_t gy_elems, int64_t ktiles, lr::FwdParam
         if (plan->d_gy) cudaFree(plan->d_gy);
         plan->d_gy = nullptr;
         plan->gy_cap = 0;
-        cudaError_t e = cudaMalloc(&plan->d_gy, sizeof(double) * (size_t)gy_elems);
+        cudaError_t e = lr::dev_malloc((void **)&plan->d_gy, sizeof(double) * (size_t)gy_elems);
         if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LR_ERR_OOM : cuda_fail(plan->ctx, e);
         plan->gy_cap = gy_elems;
     }
@@ -536,7 +558,7 @@ int backward_setup(lr_plan *plan, int64_t gy_elems, int64_t ktiles, lr::FwdParam
         if (plan->d_partial) cudaFree(plan->d_partial);
         plan->d_partial = nullptr;
         plan->partial_cap = 0;
-        cudaError_t e = cudaMalloc(&plan->d_partial, sizeof(double) * (size_t)(3 * ktiles));
+        cudaError_t e = lr::dev_malloc((void **)&plan->d_partial, sizeof(double) * (size_t)(3 * ktiles));
         if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LR_ERR_OOM : cuda_fail(plan->ctx, e);
         plan->partial_cap = 3 * ktiles;
     }
@@ -635,7 +657,7 @@ LR_API int lr_response_batched(lr_plan *plan, int64_t S, const int64_t *h_off, c
         if (plan->d_tile_off) cudaFree(plan->d_tile_off);
         plan->d_tile_off = nullptr;
         plan->tile_cap = 0;
-        cudaError_t e = cudaMalloc(&plan->d_tile_off, sizeof(int64_t) * (size_t)(S + 1));
+        cudaError_t e = lr::dev_malloc((void **)&plan->d_tile_off, sizeof(int64_t) * (size_t)(S + 1));
         if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LR_ERR_OOM : cuda_fail(plan->ctx, e);
         plan->tile_cap = S + 1;
     }
@@ -711,8 +733,8 @@ LR_API int lr_backward_batched(lr_plan *plan, int64_t S, const int64_t *h_off, c
         if (plan->d_htile_off) cudaFree(plan->d_htile_off);
         plan->d_ktile_off = plan->d_htile_off = nullptr;
         plan->ktile_cap = 0;
-        e = cudaMalloc(&plan->d_ktile_off, sizeof(int64_t) * (size_t)(S + 1));
-        if (e == cudaSuccess) e = cudaMalloc(&plan->d_htile_off, sizeof(int64_t) * (size_t)(S + 1));
+        e = lr::dev_malloc((void **)&plan->d_ktile_off, sizeof(int64_t) * (size_t)(S + 1));
+        if (e == cudaSuccess) e = lr::dev_malloc((void **)&plan->d_htile_off, sizeof(int64_t) * (size_t)(S + 1));
         if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LR_ERR_OOM : cuda_fail(plan->ctx, e);
         plan->ktile_cap = S + 1;
     }
@@ -755,5 +777,33 @@ int plan_view(const lr_plan *plan, PlanView *v)
 }
 
 int plan_cuda_fail(lr_plan *plan, int cuda_error) { return cuda_fail(plan ? plan->ctx : nullptr, (cudaError_t)cuda_error); }
+
+int plan_set_tile(lr_plan *plan, int tile)
+{
+    if (!plan) return LR_ERR_INVALID_ARG;
+    if (tile < 16 || tile > 8192) return LR_ERR_RANGE;
+    FwdParams &P = plan->base;
+    const int ymax = tile + P.HL + P.HR;
+    if (plan->desc.precision == LR_MIXED &&
+        ((double)ymax * plan->desc.dt >= plan->desc.proj_orbit->dk || (double)tile * plan->desc.dt >= plan->desc.tdi_orbit->dk))
+        return LR_ERR_RANGE;
+    P.tile = tile;
+    P.ymax = ymax;
+    P.wmax = P.ymax + 2 * P.sig_b + P.lproj_b + plan->T + 4;
+    return LR_OK;
+}
+
+int plan_reserve_batch(lr_plan *plan, int64_t S)
+{
+    if (!plan) return LR_ERR_INVALID_ARG;
+    if (S + 1 <= plan->tile_cap) return LR_OK;
+    if (plan->d_tile_off) cudaFree(plan->d_tile_off);
+    plan->d_tile_off = nullptr;
+    plan->tile_cap = 0;
+    cudaError_t e = lr::dev_malloc((void **)&plan->d_tile_off, sizeof(int64_t) * (size_t)(S + 1));
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LR_ERR_OOM : cuda_fail(plan->ctx, e);
+    plan->tile_cap = S + 1;
+    return LR_OK;
+}
 
 }  // namespace lr

@@ -1,5 +1,7 @@
 // Read-only view of a plan for entry points implemented outside the plan's own file.
 #pragma once
+#include <cuda_runtime.h>
+
 #include "lr_internal.h"
 
 namespace lr {
@@ -10,6 +12,12 @@ struct PlanView {
 };
 
 int plan_view(const lr_plan *plan, PlanView *v);
+// sets the plan's tile (output samples per CTA) and the window capacities derived from it
+int plan_set_tile(lr_plan *plan, int tile);
+// makes sure the plan's batch tile table holds S+1 entries (may allocate)
+int plan_reserve_batch(lr_plan *plan, int64_t S);
+// every device allocation of the library (honours lr_debug_fail_allocations)
+cudaError_t dev_malloc(void **p, size_t bytes);
 // records a failing cudaError_t in the plan's context and returns LR_ERR_CUDA
 int plan_cuda_fail(lr_plan *plan, int cuda_error);
 

@@ -1,0 +1,205 @@
+// CUDA-graph capture of the batched response and the tile autotuner.
+//
+// Graph: an MCMC step re-evaluates the same batch shapes with new strain values; capturing the
+// batched call (tile-table kernel + persistent fused kernel) once and replaying it removes the
+// host-side launch work from every step.  The captured pointers are fixed: the caller rewrites
+// the inputs in place between replays.
+//
+// Autotuner: the fastest tile size depends on the order, the precision and the GPU; it is found
+// by timing the fused kernel on a synthetic series for a few candidate tiles, and cached in a
+// small text file keyed by (GPU name, precision, order, generation, length bucket).
+#include <cuda_runtime.h>
+#include <sys/stat.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lr_launch.h"
+#include "lr_planview.h"
+
+struct lr_graph {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+namespace {
+
+std::string cache_path()
+{
+    const char *e = std::getenv("LR_AUTOTUNE_CACHE");
+    if (e && *e) return e;
+    const char *home = std::getenv("HOME");
+    return std::string(home ? home : "/tmp") + "/.cache/lisaresp_autotune.txt";
+}
+
+std::string tune_key(const lr::PlanView &v, int generation, int64_t n)
+{
+    cudaDeviceProp prop;
+    std::memset(&prop, 0, sizeof(prop));
+    cudaGetDeviceProperties(&prop, v.device);
+    std::string name = prop.name;
+    for (char &c : name)
+        if (c == ' ') c = '_';
+    int bucket = n > 0 ? (int)std::floor(std::log2((double)n)) : 0;
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "%s|p%d|o%d|g%d|b%d", name.c_str(), v.precision, v.order, generation, bucket);
+    return buf;
+}
+
+int cache_lookup(const std::string &key)
+{
+    FILE *f = std::fopen(cache_path().c_str(), "r");
+    if (!f) return 0;
+    char k[256];
+    int tile = 0, found = 0;
+    double ms;
+    while (std::fscanf(f, "%255s %d %lf", k, &tile, &ms) == 3)
+        if (key == k) found = tile;  // the last entry for a key wins
+    std::fclose(f);
+    return found;
+}
+
+void cache_store(const std::string &key, int tile, double ms)
+{
+    std::string path = cache_path();
+    const size_t cut = path.find_last_of('/');
+    if (cut != std::string::npos && cut > 0) mkdir(path.substr(0, cut).c_str(), 0755);  // best effort
+    FILE *f = std::fopen(path.c_str(), "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d %.6f\n", key.c_str(), tile, ms);
+    std::fclose(f);
+}
+
+}  // namespace
+
+extern "C" {
+
+LR_API int lr_response_batched_graph(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
+                                     const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
+                                     double *xyz, lr_graph **out)
+{
+    if (!plan || !out) return LR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (S < 1) return LR_ERR_INVALID_ARG;
+    if (S > (int64_t)1 << 24) return LR_ERR_RANGE;
+    int st = lr::plan_reserve_batch(plan, S);  // nothing may allocate during the capture
+    if (st) return st;
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return lr::plan_cuda_fail(plan, e);
+    lr_graph *g = new lr_graph();
+    g->graph = nullptr;
+    g->exec = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        st = lr_response_batched(plan, S, h_off, out_off, t0_h, sky, hp, hc, xyz, cs);
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g->graph);
+        if (st == LR_OK && e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess && st == LR_OK) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    cudaStreamDestroy(cs);
+    if (st != LR_OK || e != cudaSuccess) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return st != LR_OK ? st : lr::plan_cuda_fail(plan, e);
+    }
+    *out = g;
+    return LR_OK;
+}
+
+LR_API int lr_graph_launch(lr_graph *graph, void *stream)
+{
+    if (!graph || !graph->exec) return LR_ERR_INVALID_ARG;
+    return cudaGraphLaunch(graph->exec, (cudaStream_t)stream) == cudaSuccess ? LR_OK : LR_ERR_CUDA;
+}
+
+LR_API int lr_graph_destroy(lr_graph *graph)
+{
+    if (!graph) return LR_ERR_INVALID_ARG;
+    if (graph->exec) cudaGraphExecDestroy(graph->exec);
+    if (graph->graph) cudaGraphDestroy(graph->graph);
+    delete graph;
+    return LR_OK;
+}
+
+LR_API int lr_plan_autotune(lr_plan *plan, int64_t n_samples, int use_cache, void *stream, int *tile_out)
+{
+    if (!plan || !tile_out) return LR_ERR_INVALID_ARG;
+    if (n_samples < 1024 || n_samples > ((int64_t)1 << 28)) return LR_ERR_RANGE;
+    lr::PlanView v;
+    int st = lr::plan_view(plan, &v);
+    if (st) return st;
+    const int generation = v.base.q_terms == 3 ? 1 : 2;
+    const std::string key = tune_key(v, generation, n_samples);
+    if (use_cache) {
+        int t = cache_lookup(key);
+        if (t > 0 && lr::plan_set_tile(plan, t) == LR_OK) {
+            *tile_out = t;
+            return LR_OK;
+        }
+    }
+    std::vector<int> cand;
+    const int halo = v.base.HL + v.base.HR;
+    if (v.precision == LR_MIXED) {
+        for (int k = 1; k <= 3; ++k)
+            if (k * lr::MIXED_THREADS - halo >= 32) cand.push_back(k * lr::MIXED_THREADS - halo);
+    } else {
+        for (int t : {256, 384, 512, 768, 1024}) cand.push_back(t);
+    }
+    // synthetic single-source problem with all the input margins the plan needs
+    const int64_t left = v.base.sig_b + v.base.lproj_b + v.order / 2 + 4, right = v.base.sig_b + v.order / 2 + 4;
+    const int64_t nh = n_samples + left + right;
+    double *h = nullptr, *out = nullptr;
+    cudaError_t e = lr::dev_malloc((void **)&h, sizeof(double) * (size_t)nh);
+    if (e == cudaSuccess) e = lr::dev_malloc((void **)&out, sizeof(double) * 3 * (size_t)n_samples);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h, 0, sizeof(double) * (size_t)nh, (cudaStream_t)stream);
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    const int tile0 = v.base.tile;
+    int best = tile0;
+    double best_ms = 1e300;
+    // time a plan-sized single-source call: build the launch as lr_response would
+    for (size_t i = 0; e == cudaSuccess && i < cand.size(); ++i) {
+        if (lr::plan_set_tile(plan, cand[i]) != LR_OK) continue;
+        lr::PlanView w;
+        lr::plan_view(plan, &w);
+        lr::FwdParams P = w.base;
+        P.src.n1 = n_samples;
+        P.src.nh1 = nh;
+        P.src.t0h1 = P.t0 - (double)left * P.dt;
+        P.src.sky1 = lr_sky{1.0, 0.3, 0.4};
+        P.hp = h;
+        P.hc = h;
+        P.out = out;
+        P.total_tiles = (n_samples + P.tile - 1) / P.tile;
+        int le = lr::launch_forward(w.precision, lr::KIND_FUSED, w.order, P, w.threads, w.sms, stream);
+        if (le) continue;  // e.g. the tile needs more shared memory than a CTA may have
+        cudaEventRecord(a, (cudaStream_t)stream);
+        for (int r = 0; r < 3; ++r) lr::launch_forward(w.precision, lr::KIND_FUSED, w.order, P, w.threads, w.sms, stream);
+        cudaEventRecord(b, (cudaStream_t)stream);
+        e = cudaEventSynchronize(b);
+        float ms = 0.0f;
+        if (e == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+        if (e == cudaSuccess && ms / 3.0 < best_ms) {
+            best_ms = ms / 3.0;
+            best = cand[i];
+        }
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (h) cudaFree(h);
+    if (out) cudaFree(out);
+    lr::plan_set_tile(plan, best_ms < 1e300 ? best : tile0);
+    if (e != cudaSuccess) return lr::plan_cuda_fail(plan, e);
+    if (best_ms < 1e300 && use_cache) cache_store(key, best, best_ms);
+    *tile_out = best_ms < 1e300 ? best : tile0;
+    return LR_OK;
+}
+
+}  // extern "C"
