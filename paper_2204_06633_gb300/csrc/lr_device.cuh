@@ -8,28 +8,6 @@
 
 namespace lr {
 
-// ---------------------------------------------------------------- sky frame
-// k = -e_r, u = -e_phi, v = -e_theta of the SSB basis (Sec. "Reference frames"); c2p, s2p
-// rotate the antenna patterns by 2 psi.
-struct SkyConst {
-    double k[3], u[3], v[3];
-    double c2p, s2p;
-};
-
-__device__ inline SkyConst make_sky(const lr_sky &s)
-{
-    SkyConst c;
-    double sl, cl, sb, cb, s2, c2;
-    sincos(s.lam, &sl, &cl);
-    sincos(s.beta, &sb, &cb);
-    sincos(2.0 * s.psi, &s2, &c2);
-    c.k[0] = -cb * cl; c.k[1] = -cb * sl; c.k[2] = -sb;
-    c.u[0] = sl;       c.u[1] = -cl;      c.u[2] = 0.0;
-    c.v[0] = -sb * cl; c.v[1] = -sb * sl; c.v[2] = cb;
-    c.c2p = c2; c.s2p = s2;
-    return c;
-}
-
 // ---------------------------------------------------------------- splines
 struct alignas(32) Coef4 {
     double a, b, c, d;

@@ -1,20 +1,31 @@
 // Mixed-precision forward kernels (FP32 taps and accumulation of the interpolated strain,
-// float-float link series and TDI sums, FP64 for times, spline and delay evaluation).
+// float-float link series and TDI sums, FP64 for times, the orbit splines and the delays).
 //
-// Per tile of output samples a CTA
-//  1. builds, in FP64, the cubic of every read position (3 reception reads, 6 emission reads)
-//     and of every TDI delay over the tile's knot interval(s) - exact re-expansions of the orbit
-//     splines - and fits the 12 smooth geometry factors den_l * xi_l over the tile;
-//  2. stages the strain window scaled by a power of two (so FP32 never underflows), as
-//     float-float values and first differences plus second and third differences;
-//  3. computes the six link series of the tile and its TDI halo in float-float (compensated
-//     reads, see lr_mixed.cuh) and stages them the same way;
-//  4. forms X, Y, Z: per sample the chained delays are exact 64-bit fixed-point sums of the
-//     FP64-evaluated delays, split exactly into index and fraction; the FP32 correction
-//     weights come from a first-order expansion around the tile's reference delay (exact
-//     weights where the integer index differs from the reference).
-// The default tile makes the link span (tile + halo) exactly one pass of the CTA's threads.
+// A CTA of 256 threads walks tiles of output samples; per tile it runs these phases, each
+// ended by a barrier:
+//  setup    FP64: each of the 9 strain read positions (3 reception reads, 6 emission reads,
+//           Eq. for y_slr) and each of the 6 link delays re-expanded from the orbit spline as a
+//           cubic around the tile centre, held as a 64-bit fixed-point value and slope plus an
+//           FP32 remainder polynomial; 12 geometry factors den_l xi_l sampled for a cubic fit.
+//  stage    the strain window (TDI-only launches: the link series) in FP64 and its maximum;
+//           the reference fraction of every delayed TDI term and its correction weights.
+//  convert  scaled by a power of two to float-float, in the 8-phase layout.
+//  tables   first, second and third differences of the staged series.
+//  project  work item = one read position x 8 consecutive samples: exact fixed-point positions
+//           and index splits, one set of correction weights and its exact derivative per item
+//           (the fraction drifts by the Doppler rate ~1e-4 per sample), an FIR over a register
+//           window of third differences, a float-float anchor; both polarisations.
+//  links    y_l = c+_l (h+(emission) - h+(reception)) + cx_l (hx(emission) - hx(reception)) in
+//           float-float, in place; the per-sample link delays of the tile in fixed point.
+//  tables   of the six link series.
+//  TDI      work item = one channel x 4 consecutive outputs: both Michelson chains summed into
+//           one compensated accumulator; each delayed read uses the tile reference weights and
+//           their derivative (a first-order expansion in the fraction, which drifts by ~1e-7 per
+//           sample), a register window of third differences and a float-float anchor.
+// Reads whose integer index does not follow the item's pattern (an index step inside an item,
+// a knot of the orbit spline inside a projection item) take an exact per-sample path.
 #include <cuda_runtime.h>
+#include <limits.h>
 
 #include "lr_device.cuh"
 #include "lr_mixed.cuh"
@@ -26,37 +37,81 @@ __constant__ TdiTab c_tdimx = make_tdi_tab();
 
 constexpr int NTERM = 42;  // 3 channels x 2 chains x 7 delayed terms
 constexpr float TAU_UNIT = 0x1p-10f;
-constexpr float ETA = 0x1p-8f;  // half step of the central difference of the correction weights
+constexpr int PB = 8;             // samples per projection item
+constexpr int TB = MX_TDI_BLOCK;  // outputs per TDI item
+constexpr int RLW = MX_AW / 8, RLY = MX_AY / 8;
+// shared-memory regions (floats)
+constexpr int OFF_W = 0;                    // strain tables: 2 polarisations x 7 arrays
+constexpr int OFF_Y = 14 * MX_AW;           // link tables 6 x 6 arrays (staged reads before them)
+constexpr int OFF_TW = OFF_Y + 36 * MX_AY;  // TDI correction weights (U, dU/deps) per term
+// delay tables of a tile's outputs (in the strain region once the projection is done): the link
+// delay at the first output of each TDI item (int64, fixed point) and the increments within
+// the item (FP32: differences of at most 3 samples, exact integers in units of 2^-44)
+constexpr int LB = MX_YCAP / TB;  // items per row
+constexpr int LT = MX_YCAP;       // outputs per row
+static_assert(OFF_TW % 4 == 0, "weights must be 16-byte aligned");
+static_assert(2 * MX_WCAP * 2 <= 36 * MX_AY, "FP64 strain staging fits the link region");
+static_assert(6 * MX_YCAP * 2 <= 14 * MX_AW, "FP64 link staging fits the strain region");
+static_assert(6 * LB * 2 + 6 * LT <= 14 * MX_AW, "the delay tables fit the strain region");
+
+// packed pairs of FP32 values and their fused multiply-add (fma.rn.f32x2: two IEEE FMAs in one
+// instruction)
+__device__ __forceinline__ unsigned long long f2pack(float a, float b)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+__device__ __forceinline__ void f2unpack(unsigned long long r, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+enum { A_SHI = 0, A_SLO, A_DHI, A_DLO, A_A, A_E, A_ALO };
+
+__device__ __forceinline__ int phw(int j) { return (j & 7) * RLW + (j >> 3); }
+__device__ __forceinline__ int phy(int j) { return (j & 7) * RLY + (j >> 3); }
+__host__ __device__ constexpr int warr(int pol, int k) { return OFF_W + (7 * pol + k) * MX_AW; }
+__device__ __forceinline__ int ybase(int l) { return OFF_Y + 6 * l * MX_AY; }
+
+// x(j) = Xc + (j - jc) Vc + rem(r),  rem(r) = r (v + r (a2 + r a3)),  r = j - jc, in units of 2^-44
+struct PosPiece {
+    long long Xc, Vc;
+    float v, a2, a3, pad;
+};
 
 struct MxShared {
     TileInfo ti;
+    int64_t s_hint;  // source of the CTA's previous tile
     SkyConst sk;
-    int64_t k_lo, w_lo;
-    int ny, wlen;
+    int64_t k_lo;
+    int ny;
     double u0;
-    double scale, unscale;
     unsigned long long maxbits;
-    // reading positions (window-local, fixed point) as cubics in the knot coordinate
-    double rp[2][9][4];
-    double xa[2];
-    double rstep;
-    int jsw;
-    // TDI delays (fixed point samples) as cubics, over the output tile
-    double dp[2][6][4];
-    double xta[2];
-    double rstep_t;
-    int jswt;
+    int wlo, whi;  // extent of the read positions over the span (tile-local samples)
+    // read positions: [piece][read], tile-local (strain index - k_lo)
+    PosPiece pp[2][9];
+    int jsw, jc;
+    // link delays in samples: [piece][link], output-local index
+    PosPiece dp[2][6];
+    int jswt, ic;
     // geometry factors c+_l, cx_l as cubics in tau = (j - jc) 2^-10
     double gnode[4][12];
-    double tmax;
-    float g0h[12], g0l[12], g1h[12], g1l[12], g2[12], g3[12];
-    int jc;
-    // TDI reference per term
+    double tmax, inv_tmax;
+    float g0h[12], g0l[12], g1h[12], g2[12], g3[12];
+    // TDI reference per delayed term
     int tfm[NTERM];
-    float tehi[NTERM], telo[NTERM];
+    float tehi[NTERM];
 };
 
-// ---------------------------------------------------------------- per-tile setup helpers
+// ---------------------------------------------------------------- helpers
 __device__ inline const double *orbit_coef_ptr(const OrbitDev &o, int K, int s)
 {
     return o.coef + ((size_t)K * NSERIES + s) * 4;
@@ -71,68 +126,119 @@ __device__ inline int clampK(const OrbitDev &o, double u)
 
 __device__ inline double horner3(const double *c, double x) { return fma(x, fma(x, fma(x, c[3], c[2]), c[1]), c[0]); }
 
-// float-float value of a fitted geometry factor at tau
+// knot-piece switch: first index of [0, n) that lies in the piece after the one at index 0
+__device__ inline int piece_switch(double ua, double rstep, int K0, int K1, int n)
+{
+    if (K1 == K0) return n;
+    double jj = ceil(((double)K1 - ua) / rstep);
+    return jj < 0 ? 0 : (jj > n ? n : (int)jj);
+}
+
+// the cubic c(x), x = xa + j rstep, re-expanded around j = jc in powers of (j - jc):
+// value, first, second/2 and third/6 derivative in j
+__device__ inline void reexpand(const double *c, double xa, double rstep, int jc, double *d)
+{
+    const double x = fma((double)jc, rstep, xa);
+    d[0] = horner3(c, x);
+    d[1] = fma(x, fma(x, 3.0 * c[3], 2.0 * c[2]), c[1]) * rstep;
+    d[2] = fma(x, 3.0 * c[3], c[2]) * rstep * rstep;
+    d[3] = c[3] * rstep * rstep * rstep;
+}
+
+__device__ inline PosPiece make_piece(double P0, double P1, double P2, double P3)
+{
+    PosPiece p;
+    p.Xc = __double2ll_rn(P0 * FX_ONE);
+    p.Vc = __double2ll_rn(P1 * FX_ONE);
+    p.v = (float)(P1 * FX_ONE - (double)p.Vc);
+    p.a2 = (float)(P2 * FX_ONE);
+    p.a3 = (float)(P3 * FX_ONE);
+    p.pad = 0.0f;
+    return p;
+}
+
+// remainder of a piece at r = j - jc (rf = r as float)
+__device__ __forceinline__ long long piece_rem(const PosPiece &p, float rf)
+{
+    return (long long)__float2int_rn(rf * fmaf(rf, fmaf(rf, p.a3, p.a2), p.v));
+}
+
+__device__ __forceinline__ long long piece_at(const PosPiece &p, int r)
+{
+    return p.Xc + (long long)r * p.Vc + piece_rem(p, (float)r);
+}
+
+// Tile g of the launch: its source, offsets and sky frame.  In a batch the source is found by
+// galloping forward from s_hint, the source of the CTA's previous tile (a CTA's tiles come in
+// increasing order), then bisecting; the loops are bounded by the 64-bit index width.
+__device__ inline void mx_tile(const FwdParams &P, int64_t g, int ochan, int64_t &s_hint, TileInfo &ti,
+                               SkyConst &sk)
+{
+    ti.ok = 1;
+    if (P.src.tile_off == nullptr) {
+        ti.N = P.src.n1;
+        ti.nh = P.src.nh1;
+        ti.t0h = P.src.t0h1;
+        ti.sky = P.src.sky1;
+        ti.hp = P.hp;
+        ti.hc = P.hc;
+        ti.out = P.out;
+        ti.yin = P.yin;
+        ti.n0 = g * P.tile;
+        sk = P.src.skyc1;
+    } else {
+        const int64_t *to = P.src.tile_off;
+        const int64_t S = P.src.S;
+        int64_t lo = s_hint;
+        if (lo < 0 || lo >= S || __ldg(to + lo) > g) lo = 0;
+        int64_t step = 1, hi = lo + 1;
+        while (hi < S && __ldg(to + hi) <= g) {  // to[lo] <= g throughout
+            lo = hi;
+            step <<= 1;
+            hi = lo + step;
+        }
+        if (hi > S) hi = S;
+        while (hi - lo > 1) {  // to[lo] <= g < to[hi]
+            const int64_t mid = (lo + hi) >> 1;
+            if (__ldg(to + mid) <= g) lo = mid; else hi = mid;
+        }
+        const int64_t s = lo;
+        s_hint = s;
+        const int64_t ho = __ldg(P.src.h_off + s), ho1 = __ldg(P.src.h_off + s + 1);
+        const int64_t oo = __ldg(P.src.out_off + s), oo1 = __ldg(P.src.out_off + s + 1);
+        ti.N = oo1 - oo;
+        ti.nh = ho1 - ho;
+        if (ti.N < 0 || ti.nh < 0) ti.ok = 0;
+        ti.t0h = __ldg(P.src.t0h + s);
+        ti.sky = P.src.sky[s];
+        ti.hp = P.hp + ho;
+        ti.hc = P.hc + ho;
+        ti.out = P.out + ochan * oo;
+        ti.yin = P.yin ? P.yin + 6 * oo : nullptr;
+        ti.n0 = (g - __ldg(to + s)) * P.tile;
+        sk = P.src.skyc[s];
+    }
+    const int64_t rem = ti.N - ti.n0;
+    ti.nb = rem < P.tile ? rem : P.tile;
+    if (ti.nb < 0) ti.nb = 0;
+}
+
+// value of a fitted geometry factor at tau: the constant in float-float, the variation over the
+// tile (a relative 1e-4 at most) in FP32
 __device__ __forceinline__ ff geom_at(const MxShared &sh, int f, float tau)
 {
-    ff c = ff_add({sh.g0h[f], sh.g0l[f]}, ff_mul_f({sh.g1h[f], sh.g1l[f]}, tau));
-    return ff_add_f(c, tau * tau * fmaf(tau, sh.g3[f], sh.g2[f]));
+    return ff_add_f({sh.g0h[f], sh.g0l[f]}, tau * fmaf(tau, fmaf(tau, sh.g3[f], sh.g2[f]), sh.g1h[f]));
 }
 
-// Difference tables from float-float values held in S.shi / S.slo.  Entries whose difference
-// stencils leave the window are set to 0 (they are never read).
-__device__ void build_tables_ff(int len, const CompSeries &S)
+// block max of the bit patterns b of |v| (for non-negative doubles the order of the patterns is
+// the order of the values; a NaN orders above every finite value)
+__device__ __forceinline__ unsigned long long abs_bits(double v)
 {
-    for (int j = threadIdx.x; j < len; j += blockDim.x) {
-        ff s0 = {S.shi[j], S.slo[j]};
-        float dh = 0.0f, dl = 0.0f, a = 0.0f, al = 0.0f, e = 0.0f;
-        if (j + 1 < len) {
-            ff s1 = {S.shi[j + 1], S.slo[j + 1]};
-            ff d1 = ff_sub(s1, s0);
-            dh = d1.hi;
-            dl = d1.lo;
-            if (j >= 1) {
-                ff sm = {S.shi[j - 1], S.slo[j - 1]};
-                ff dd = ff_sub(d1, ff_sub(s0, sm));
-                a = 0.5f * dd.hi;
-                al = 0.5f * dd.lo;
-            }
-            if (j + 3 < len) {
-                ff s2 = {S.shi[j + 2], S.slo[j + 2]}, s3 = {S.shi[j + 3], S.slo[j + 3]};
-                ff d2 = ff_sub(s2, s1), d3 = ff_sub(s3, s2);
-                ff e3 = ff_sub(ff_sub(d3, d2), ff_sub(d2, d1));
-                e = e3.hi + e3.lo;
-            }
-        }
-        S.dhi[j] = dh;
-        S.dlo[j] = dl;
-        S.e[j] = e;
-        if (S.alo) {
-            S.a[j] = a;
-            S.alo[j] = al;
-        } else {
-            S.a[j] = a + al;
-        }
-    }
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
 }
 
-// link-series tables: 6 arrays of `stride` floats; strain tables add the low part of a (7 arrays)
-__device__ inline CompSeries series_at(float *base, int stride, bool with_alo = false)
+__device__ inline void block_absmax(unsigned long long *dst, unsigned long long b)
 {
-    CompSeries S;
-    S.shi = base;
-    S.slo = base + stride;
-    S.dhi = base + 2 * stride;
-    S.dlo = base + 3 * stride;
-    S.a = base + 4 * stride;
-    S.e = base + 5 * stride;
-    S.alo = with_alo ? base + 6 * stride : nullptr;
-    return S;
-}
-
-// block max of |v| as the bit pattern of a non-negative double
-__device__ inline void block_absmax(unsigned long long *dst, double v)
-{
-    unsigned long long b = (unsigned long long)__double_as_longlong(fabs(v));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         unsigned long long c = __shfl_xor_sync(0xffffffffu, b, o);
@@ -141,35 +247,92 @@ __device__ inline void block_absmax(unsigned long long *dst, double v)
     if ((threadIdx.x & 31) == 0) atomicMax(dst, b);
 }
 
-__device__ inline void set_scale(MxShared &sh)
+// power-of-two scale putting the tile's largest value in [1/2, 1), built from the exponent
+// bits of the maximum (integer work only); 1 for a zero, subnormal or non-finite maximum
+__device__ __forceinline__ void tile_scale(unsigned long long maxbits, double &scale, double &unscale)
 {
-    double mx = __longlong_as_double((long long)sh.maxbits);
-    if (mx > 0.0 && isfinite(mx)) {
-        int E;
-        frexp(mx, &E);
-        sh.scale = ldexp(1.0, -E);
-        sh.unscale = ldexp(1.0, E);
-    } else {
-        sh.scale = 1.0;
-        sh.unscale = 1.0;
+    const long long eb = (long long)((maxbits >> 52) & 0x7ffull);  // max = f 2^(eb - 1022), f in [1/2, 1)
+    const bool ok = eb >= 1 && eb <= 2044;
+    scale = ok ? __longlong_as_double((2045 - eb) << 52) : 1.0;
+    unscale = ok ? __longlong_as_double((eb + 1) << 52) : 1.0;
+}
+
+// Difference tables of a staged float-float series (arrays at base + k * AS, 8-phase index
+// with row length RL): d = s_{j+1} - s_j and a = (d_j - d_{j-1})/2 in float-float (ALO: the low
+// part of a kept in its own array, else folded into a), e = d_{j+2} - 2 d_{j+1} + d_j in FP32.
+// Each thread forms 4 consecutive entries of one of the nser series (series stride SS) from one
+// set of differences.  Entries whose stencils leave [0, len) are 0; no read ever uses them.
+template <bool ALO, int RL>
+__device__ void build_tables(float *smf, int base0, int AS, int SS, int nser, int len)
+{
+    auto at = [](int i) { return (i & 7) * RL + (i >> 3); };
+    const int nq = (len + 3) / 4;
+    for (int it = threadIdx.x; it < nser * nq; it += blockDim.x) {
+        const int ser = it / nq, t = it - ser * nq;
+        const int base = base0 + ser * SS;
+        const int j0 = 4 * t;
+        ff s[8];  // s_{j0-1} .. s_{j0+6}
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = j0 - 1 + u;
+            s[u] = (i >= 0 && i < len) ? ff{smf[base + at(i)], smf[base + AS + at(i)]} : ff{0.0f, 0.0f};
+        }
+        ff d[7], dd[6];  // d_{j0-1+u}, dd_{j0-1+u} = d_{j0+u} - d_{j0-1+u}
+#pragma unroll
+        for (int u = 0; u < 7; ++u) d[u] = ff_sub(s[u + 1], s[u]);
+#pragma unroll
+        for (int u = 0; u < 6; ++u) dd[u] = ff_sub(d[u + 1], d[u]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int j = j0 + k;
+            if (j >= len) break;
+            float dh = 0.0f, dl = 0.0f, a = 0.0f, al = 0.0f, e = 0.0f;
+            if (j + 1 < len) {
+                dh = d[k + 1].hi;
+                dl = d[k + 1].lo;
+                if (j >= 1) {
+                    a = 0.5f * dd[k].hi;
+                    al = 0.5f * dd[k].lo;
+                }
+                if (j + 3 < len) {
+                    const ff e3 = ff_sub(dd[k + 2], dd[k + 1]);
+                    e = e3.hi + e3.lo;
+                }
+            }
+            const int p = at(j);
+            smf[base + A_DHI * AS + p] = dh;
+            smf[base + A_DLO * AS + p] = dl;
+            smf[base + A_E * AS + p] = e;
+            if (ALO) {
+                smf[base + A_A * AS + p] = a;
+                smf[base + A_ALO * AS + p] = al;
+            } else {
+                smf[base + A_A * AS + p] = a + al;
+            }
+        }
     }
 }
 
-// ---------------------------------------------------------------- setup phases
-// Read-position cubics (threads 0..17), knot bookkeeping (thread 18) and geometry nodes
-// (threads 32..43: node = i / 3, arm = i % 3).
-__device__ void setup_projection(const FwdParams &P, MxShared &sh)
+// ---------------------------------------------------------------- per-tile setup
+// Threads 0..17: read-position pieces [piece][read] and the span's position extent;
+// threads 32..43: link-delay pieces [piece][link]; threads 64..75: geometry nodes.
+template <int KIND>
+__device__ void setup_tile(const FwdParams &P, MxShared &sh)
 {
     const int tid = threadIdx.x;
-    const OrbitDev &o = P.po;
-    const double ua = (P.t0 + (double)sh.k_lo * P.dt - o.t_first) * o.inv_dk;
-    const double ub = ua + (double)(sh.ny - 1) * P.dt * o.inv_dk;
-    const int K0 = clampK(o, ua), K1 = clampK(o, ub);
-    if (tid < 18) {
+    if (KIND != KIND_TDI && tid < 18) {
+        const OrbitDev &o = P.po;
+        const int ny = sh.ny;
+        const double rstep = P.dt * o.inv_dk;
+        const double ua = (P.t0 + (double)sh.k_lo * P.dt - o.t_first) * o.inv_dk;
+        const double ub = ua + (double)(ny - 1) * rstep;
+        const int K0 = clampK(o, ua), K1 = clampK(o, ub);
+        const int jsw = piece_switch(ua, rstep, K0, K1, ny);
         const int iv = tid / 9, rd = tid % 9;
         const int K = iv == 0 ? K0 : K1;
+        const double xa = ua - (double)K;
         // emission reads (rd >= 3) of link l = rd - 3 shift by the emitter's k.x/c and L_l;
-        // reception reads by the receiver's k.x/c
+        // reception reads by the receiver's k.x/c.  position(j) = j + u0 - c(x(j)) samples
         const int sc = rd < 3 ? rd : (rd == 3 ? 1 : rd == 4 ? 2 : rd == 5 ? 0 : rd == 6 ? 2 : rd == 7 ? 1 : 0);
         double c[4] = {0.0, 0.0, 0.0, 0.0};
         const double kc = 1.0 / (C_LIGHT * P.dt);
@@ -181,27 +344,54 @@ __device__ void setup_projection(const FwdParams &P, MxShared &sh)
             const double *q = orbit_coef_ptr(o, K, 9 + rd - 3);
             for (int i = 0; i < 4; ++i) c[i] = fma(q[i], P.inv_dt, c[i]);
         }
-        const double base = (double)(sh.k_lo - sh.w_lo) + sh.u0;
-        sh.rp[iv][rd][0] = (base - c[0]) * FX_ONE;
-        for (int i = 1; i < 4; ++i) sh.rp[iv][rd][i] = -c[i] * FX_ONE;
-    } else if (tid == 18) {
-        sh.xa[0] = ua - (double)K0;
-        sh.xa[1] = ua - (double)K1;
-        sh.rstep = P.dt * o.inv_dk;
-        int jsw = sh.ny;
-        if (K1 != K0) {
-            double jj = ceil(((double)K1 - ua) / sh.rstep);
-            jsw = jj < 0 ? 0 : (jj > sh.ny ? sh.ny : (int)jj);
+        const int jc = ny / 2;
+        double d[4];
+        reexpand(c, xa, rstep, jc, d);
+        sh.pp[iv][rd] = make_piece((double)jc + sh.u0 - d[0], 1.0 - d[1], -d[2], -d[3]);
+        // extent of the positions (increasing in j) at the span ends, on the piece holding them
+        if ((0 < jsw) == (iv == 0)) {
+            double p = sh.u0 - horner3(c, xa);
+            p = fmin(fmax(p, -1e8), 1e8);
+            atomicMin(&sh.wlo, (int)floor(p));
         }
-        sh.jsw = jsw;
-        sh.jc = sh.ny / 2;
-        sh.tmax = ((double)(sh.ny / 2) + 1.0) * (double)TAU_UNIT;
-    } else if (tid >= 32 && tid < 44) {
+        if ((ny - 1 < jsw) == (iv == 0)) {
+            double p = (double)(ny - 1) + sh.u0 - horner3(c, fma((double)(ny - 1), rstep, xa));
+            p = fmin(fmax(p, -1e8), 1e8);
+            atomicMax(&sh.whi, (int)floor(p));
+        }
+        if (tid == 0) {
+            sh.jsw = jsw;
+            sh.jc = jc;
+            sh.tmax = ((double)jc + 1.0) * (double)TAU_UNIT;
+            sh.inv_tmax = 1.0 / sh.tmax;
+        }
+    } else if (KIND != KIND_PROJECT && tid >= 32 && tid < 44) {
+        const OrbitDev &o = P.to;
+        const int nb = (int)sh.ti.nb;
+        const double rs = P.dt * o.inv_dk;
+        const double ua = (P.t0 + (double)sh.ti.n0 * P.dt - o.t_first) * o.inv_dk;
+        const double ub = ua + (double)(nb - 1) * rs;
+        const int K0 = clampK(o, ua), K1 = clampK(o, ub);
+        const int iv = (tid - 32) / 6, l = (tid - 32) % 6;
+        const int K = iv == 0 ? K0 : K1;
+        const double *q = orbit_coef_ptr(o, K, 9 + l);
+        double c[4];
+        for (int i = 0; i < 4; ++i) c[i] = q[i] * P.inv_dt;
+        const int ic = nb / 2;
+        double d[4];
+        reexpand(c, ua - (double)K, rs, ic, d);
+        sh.dp[iv][l] = make_piece(d[0], d[1], d[2], d[3]);
+        if (tid == 32) {
+            sh.jswt = piece_switch(ua, rs, K0, K1, nb);
+            sh.ic = ic;
+        }
+    } else if (KIND != KIND_TDI && tid >= 64 && tid < 76) {
         // geometry factors of arm a at Chebyshev node i (Eq. projected-strain-ssb patterns,
         // psi rotation, 1/(2(1 -+ k.n)) for the two directions)
-        const int i = (tid - 32) / 3, a = (tid - 32) % 3;
+        const OrbitDev &o = P.po;
+        const int i = (tid - 64) / 3, a = (tid - 64) % 3;
         const double tmax = ((double)(sh.ny / 2) + 1.0) * (double)TAU_UNIT;
-        const double tau = tmax * cos((2.0 * i + 1.0) * 3.14159265358979323846 / 8.0);
+        const double tau = tmax * P.cheb_node[i];
         const double t = P.t0 + ((double)(sh.k_lo + sh.ny / 2) + tau / (double)TAU_UNIT) * P.dt;
         double x;
         const Coef4 *row = spline_row(o, t, &x);
@@ -209,14 +399,16 @@ __device__ void setup_projection(const FwdParams &P, MxShared &sh)
         double d[3];
         for (int c = 0; c < 3; ++c) d[c] = cubic(ldg4(row + 3 * r + c), x) - cubic(ldg4(row + 3 * s + c), x);
         const SkyConst &S = sh.sk;
-        double inv = 1.0 / sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        double n0 = d[0] * inv, n1 = d[1] * inv, n2 = d[2] * inv;
-        double un = S.u[0] * n0 + S.u[1] * n1 + S.u[2] * n2;
-        double vn = S.v[0] * n0 + S.v[1] * n1 + S.v[2] * n2;
-        double kn = S.k[0] * n0 + S.k[1] * n1 + S.k[2] * n2;
-        double xip = un * un - vn * vn, xic = 2.0 * un * vn;
-        double xp = S.c2p * xip + S.s2p * xic, xc = -S.s2p * xip + S.c2p * xic;
-        double df = 0.5 / (1.0 - kn), dr = 0.5 / (1.0 + kn);
+        const double inv = rsqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        const double n0 = d[0] * inv, n1 = d[1] * inv, n2 = d[2] * inv;
+        const double un = S.u[0] * n0 + S.u[1] * n1 + S.u[2] * n2;
+        const double vn = S.v[0] * n0 + S.v[1] * n1 + S.v[2] * n2;
+        const double kn = S.k[0] * n0 + S.k[1] * n1 + S.k[2] * n2;
+        const double xip = un * un - vn * vn, xic = 2.0 * un * vn;
+        const double xp = S.c2p * xip + S.s2p * xic, xc = -S.s2p * xip + S.c2p * xic;
+        // 1/(2(1 - kn)) and 1/(2(1 + kn)) from one division
+        const double den = 0.5 / ((1.0 - kn) * (1.0 + kn));
+        const double df = (1.0 + kn) * den, dr = (1.0 - kn) * den;
         sh.gnode[i][a] = xp * df;
         sh.gnode[i][6 + a] = xc * df;
         sh.gnode[i][5 - a] = xp * dr;
@@ -225,10 +417,10 @@ __device__ void setup_projection(const FwdParams &P, MxShared &sh)
 }
 
 // cubic through the 4 geometry nodes: monomial coefficients in tau from the Chebyshev
-// inverse Vandermonde (threads 64..75)
+// inverse Vandermonde (threads 96..107)
 __device__ void fit_geometry(const FwdParams &P, MxShared &sh)
 {
-    const int f = threadIdx.x - 64;
+    const int f = threadIdx.x - 96;
     if (f < 0 || f >= 12) return;
     double b[4];
     double sc = 1.0;
@@ -236,250 +428,386 @@ __device__ void fit_geometry(const FwdParams &P, MxShared &sh)
         double acc = 0.0;
         for (int i = 0; i < 4; ++i) acc = fma(P.cheb[k][i], sh.gnode[i][f], acc);
         b[k] = acc * sc;
-        sc /= sh.tmax;
+        sc *= sh.inv_tmax;
     }
-    ff c0 = ff_from_double(b[0]), c1 = ff_from_double(b[1]);
-    sh.g0h[f] = c0.hi; sh.g0l[f] = c0.lo;
-    sh.g1h[f] = c1.hi; sh.g1l[f] = c1.lo;
+    const ff c0 = ff_from_double(b[0]);
+    sh.g0h[f] = c0.hi;
+    sh.g0l[f] = c0.lo;
+    sh.g1h[f] = (float)b[1];
     sh.g2[f] = (float)b[2];
     sh.g3[f] = (float)b[3];
 }
 
-// TDI delay cubics over the output tile (fixed point, samples x 2^44): threads 96..107, 108
-__device__ void setup_tdi(const FwdParams &P, MxShared &sh, int64_t n0, int nb)
-{
-    const int tid = threadIdx.x;
-    const OrbitDev &o = P.to;
-    const double ua = (P.t0 + (double)n0 * P.dt - o.t_first) * o.inv_dk;
-    const double ub = ua + (double)(nb > 0 ? nb - 1 : 0) * P.dt * o.inv_dk;
-    const int K0 = clampK(o, ua), K1 = clampK(o, ub);
-    if (tid >= 96 && tid < 108) {
-        const int iv = (tid - 96) / 6, l = (tid - 96) % 6;
-        const double *q = orbit_coef_ptr(o, iv == 0 ? K0 : K1, 9 + l);
-        for (int i = 0; i < 4; ++i) sh.dp[iv][l][i] = q[i] * P.inv_dt * FX_ONE;
-    } else if (tid == 108) {
-        sh.xta[0] = ua - (double)K0;
-        sh.xta[1] = ua - (double)K1;
-        sh.rstep_t = P.dt * o.inv_dk;
-        int jsw = nb;
-        if (K1 != K0) {
-            double jj = ceil(((double)K1 - ua) / sh.rstep_t);
-            jsw = jj < 0 ? 0 : (jj > nb ? nb : (int)jj);
-        }
-        sh.jswt = jsw;
-    }
-}
-
-// fixed-point delays (samples x 2^44) of the six links at output index i of the tile
-__device__ __forceinline__ void tdi_delays_fx(const MxShared &sh, int i, long long &L0, long long &L1, long long &L2,
-                                              long long &L3, long long &L4, long long &L5)
-{
-    const int iv = i < sh.jswt ? 0 : 1;
-    const double x = fma((double)i, sh.rstep_t, sh.xta[iv]);
-    L0 = __double2ll_rn(horner3(sh.dp[iv][0], x));
-    L1 = __double2ll_rn(horner3(sh.dp[iv][1], x));
-    L2 = __double2ll_rn(horner3(sh.dp[iv][2], x));
-    L3 = __double2ll_rn(horner3(sh.dp[iv][3], x));
-    L4 = __double2ll_rn(horner3(sh.dp[iv][4], x));
-    L5 = __double2ll_rn(horner3(sh.dp[iv][5], x));
-}
-
-__device__ __forceinline__ long long pick(int l, long long L0, long long L1, long long L2, long long L3, long long L4,
-                                          long long L5)
-{
-    return l == 0 ? L0 : l == 1 ? L1 : l == 2 ? L2 : l == 3 ? L3 : l == 4 ? L4 : L5;
-}
-
-// Per-tile reference of each delayed TDI term at the tile centre, and its correction weights at
-// eps_ref - ETA, eps_ref, eps_ref + ETA (threads 128..253: term = i / 3, point = i % 3).
+// Reference of each delayed TDI term at the tile centre ic (its chained delay is the sum of the
+// pieces' centre values, exactly what the delay table holds at ic) and the correction weights
+// there with their derivative, interleaved as (U_a, dU_a/deps) pairs (threads 128..169).
 template <int T>
-__device__ void setup_tdi_refs(const FwdParams &P, MxShared &sh, int nb, float *tw)
+__device__ void tdi_refs(const FwdParams &P, MxShared &sh, float *tw)
 {
-    constexpr int NU = T >= 4 ? T - 3 : 1;
-    const int i = threadIdx.x - 128;
-    if (i < 0 || i >= 3 * NTERM) return;
-    const int id = i / 3, pt = i % 3;
+    const int id = threadIdx.x - 128;
+    if (id < 0 || id >= NTERM) return;
     const int ch = id / 14, c = (id / 7) % 2, q = id % 7 + 1;
     if (q > P.q_terms) return;
-    long long L0, L1, L2, L3, L4, L5;
-    tdi_delays_fx(sh, nb / 2, L0, L1, L2, L3, L4, L5);
+    const int iv = sh.ic < sh.jswt ? 0 : 1;
     long long D = 0;
-    for (int k = 1; k <= q; ++k) D += pick(chain_pair(ch, c, k), L0, L1, L2, L3, L4, L5);
-    Split s = split_fx(-D);
-    if (pt == 1) {
-        sh.tfm[id] = s.m;
-        sh.tehi[id] = s.ehi;
-        sh.telo[id] = s.elo;
-    }
+    for (int k = 1; k <= q; ++k) D += sh.dp[iv][chain_pair(ch, c, k)].Xc;
+    const int nlr = sh.ic + P.HL;
+    const Split s = split_fx(((long long)nlr << FX_BITS) - D);
+    sh.tfm[id] = s.m - nlr;
+    sh.tehi[id] = s.ehi;
+    constexpr int NUP = mx_nup(T);
+    float2 *w = reinterpret_cast<float2 *>(tw) + id * NUP;
     if constexpr (T >= 4) {
-        float U[NU];
-        comp_weights<T>(s.ehi + (float)(pt - 1) * ETA, U);
-        float *w = tw + ((size_t)id * 3 + pt) * NU;
+        constexpr int NU = T - 3;
+        float U[NU], U1[NU];
+        comp_weights_d<T>(s.ehi, U, U1);
 #pragma unroll
-        for (int a = 0; a < NU; ++a) w[a] = U[a];
+        for (int a = 0; a < NUP; ++a) w[a] = a < NU ? make_float2(U[a], U1[a]) : make_float2(0.0f, 0.0f);
+    } else {
+#pragma unroll
+        for (int a = 0; a < NUP; ++a) w[a] = make_float2(0.0f, 0.0f);
     }
 }
 
-// [U(eps - ETA), U(eps), U(eps + ETA)] -> [U(eps), dU/deps] in place
+// ---------------------------------------------------------------- projection reads
+// float-float s + eps d + eps (eps - 1) a - C of a strain series at 8-phase position ai (the
+// curvature product formed from the exact eps_hi (eps_hi - 1) against the float-float a: it
+// feeds two levels of cancellation).  The result is an unnormalised float-float pair.  Degree 1
+// (T = 2) is the linear anchor s + eps d alone.
 template <int T>
-__device__ void finish_tdi_refs(const FwdParams &P, float *tw)
+__device__ __forceinline__ ff strain_anchor(const float *smf, int pol, int ai, float eh, float el, float C)
 {
-    constexpr int NU = T >= 4 ? T - 3 : 1;
-    if constexpr (T >= 4) {
-        for (int idx = threadIdx.x; idx < NTERM * NU; idx += blockDim.x) {
-            const int id = idx / NU, a = idx % NU;
-            if (id % 7 + 1 > P.q_terms) continue;
-            float *w = tw + (size_t)id * 3 * NU;
-            float um = w[a], u0 = w[NU + a], up = w[2 * NU + a];
-            w[a] = u0;
-            w[NU + a] = (up - um) * (0.5f / ETA);
+    if constexpr (T < 4) {
+        const float shi = smf[warr(pol, A_SHI) + ai], slo = smf[warr(pol, A_SLO) + ai];
+        const float dhi = smf[warr(pol, A_DHI) + ai], dlo = smf[warr(pol, A_DLO) + ai];
+        const float p = eh * dhi;
+        const float pe = fmaf(eh, dhi, -p);
+        const ff t1 = two_sum(shi, p);
+        return {t1.hi, (slo + t1.lo) + (pe + fmaf(eh, dlo, el * dhi))};
+    }
+    const float shi = smf[warr(pol, A_SHI) + ai], slo = smf[warr(pol, A_SLO) + ai];
+    const float dhi = smf[warr(pol, A_DHI) + ai], dlo = smf[warr(pol, A_DLO) + ai];
+    const float ahi = smf[warr(pol, A_A) + ai], alo = smf[warr(pol, A_ALO) + ai];
+    const float p = eh * dhi;
+    const float pe = fmaf(eh, dhi, -p);
+    const float em1 = eh - 1.0f;
+    const float q = eh * em1;
+    const float qe = fmaf(el, 2.0f * eh - 1.0f, fmaf(eh, em1, -q));
+    const float cq = q * ahi;
+    const float cqe = fmaf(q, ahi, -cq);
+    const ff t1 = two_sum(shi, p);
+    const ff t2 = two_sum(t1.hi, cq);
+    const float lo = (slo + (t1.lo + t2.lo)) + (pe + fmaf(eh, dlo, el * dhi)) + (cqe + fmaf(q, alo, qe * ahi)) - C;
+    return {t2.hi, lo};
+}
+
+__device__ __forceinline__ void store_read(float *smf, int rd, int pol, int j, ff v)
+{
+    const int row = rd * 4 + pol * 2;
+    smf[OFF_Y + row * MX_AY + phy(j)] = v.hi;
+    smf[OFF_Y + (row + 1) * MX_AY + phy(j)] = v.lo;
+}
+
+// One projection item sample by sample with exact weights: items whose integer index steps
+// inside the item, or that straddle a knot of the orbit spline.  Out-of-window stencils read 0
+// and record ERR_WINDOW.
+template <int T>
+__device__ __noinline__ void proj_item_exact(float *smf, const MxShared &sh, int rd, int j0, int kmax, int wlen,
+                                             long long woff_fx, int *err)
+{
+    constexpr int h = (T - 2) / 2;
+    for (int k = 0; k < kmax; ++k) {
+        const int j = j0 + k;
+        const PosPiece p = sh.pp[j < sh.jsw ? 0 : 1][rd];
+        const Split s = split_fx(piece_at(p, j - sh.jc) - woff_fx);
+        if (s.m - h < 0 || s.m + h + 1 >= wlen) {
+            atomicOr(err, ERR_WINDOW);
+            store_read(smf, rd, 0, j, {0.0f, 0.0f});
+            store_read(smf, rd, 1, j, {0.0f, 0.0f});
+            continue;
+        }
+        float U[T >= 4 ? T - 3 : 1];
+        if constexpr (T >= 4) comp_weights<T>(s.ehi, U);
+        for (int pol = 0; pol < 2; ++pol) {
+            float C = 0.0f;
+            if constexpr (T >= 4) {
+#pragma unroll
+                for (int a = 0; a < T - 3; ++a) C = fmaf(U[a], smf[warr(pol, A_E) + phw(s.m - h + a)], C);
+            }
+            store_read(smf, rd, pol, j, strain_anchor<T>(smf, pol, phw(s.m), s.ehi, s.elo, C));
         }
     }
 }
 
-// ---------------------------------------------------------------- per-sample work
-// One compensated read of both polarisations at read `rd` (0-2: reception at spacecraft rd,
-// 3-8: emission of link rd-3) for y-local index j.  A stencil outside the staged window records
-// ERR_WINDOW and reads as zero.
+// Projection item: read rd at the samples j0 .. j0+7 of the span.
 template <int T>
-__device__ __forceinline__ void strain_read(const MxShared &sh, const CompSeries &Hp, const CompSeries &Hc, int iv,
-                                            double x, long long jfx, int rd, int *err, ff &vp, ff &vc)
+__device__ __forceinline__ void proj_item(float *smf, const MxShared &sh, int rd, int b, int ny, int wlen,
+                                          long long woff_fx, int *err)
 {
-    constexpr int NU = T >= 4 ? T - 3 : 1;
     constexpr int h = (T - 2) / 2;
-    long long X = __double2ll_rn(horner3(sh.rp[iv][rd], x)) + jfx;
-    Split s = split_fx(X);
-    if (s.m - h < 0 || s.m + h + 1 >= sh.wlen) {
-        atomicOr(err, ERR_WINDOW);
-        vp = vc = {0.0f, 0.0f};
+    constexpr int NU = T >= 4 ? T - 3 : 1;
+    constexpr int NE = NU + PB - 1;
+    const int j0 = PB * b;
+    const int kmax = min(PB, ny - j0);
+    const int piece = j0 < sh.jsw ? 0 : 1;
+    if (piece == 0 && j0 + kmax - 1 >= sh.jsw) {
+        proj_item_exact<T>(smf, sh, rd, j0, kmax, wlen, woff_fx, err);
         return;
     }
-    float U[NU];
-    if constexpr (T >= 4) comp_weights<T>(s.ehi, U);
-    vp = comp_value<T, true>(Hp, s.m, s.ehi, s.elo, U);
-    vc = comp_value<T, true>(Hc, s.m, s.ehi, s.elo, U);
-}
-
-// Six link samples (scaled, float-float) at y-local index j, handed to store(l, value):
-// y_l = c+_l (h+(emission) - h+(reception)) + cx_l (hx(emission) - hx(reception)).
-template <int T, class Store>
-__device__ void project_sample_mx(const MxShared &sh, const CompSeries &Hp, const CompSeries &Hc, int j, int *err,
-                                  Store store)
-{
-    const int iv = j < sh.jsw ? 0 : 1;
-    const double x = fma((double)j, sh.rstep, sh.xa[iv]);
-    const long long jfx = (long long)j << FX_BITS;
-    ff Rp0, Rp1, Rp2, Rc0, Rc1, Rc2;
-    strain_read<T>(sh, Hp, Hc, iv, x, jfx, 0, err, Rp0, Rc0);
-    strain_read<T>(sh, Hp, Hc, iv, x, jfx, 1, err, Rp1, Rc1);
-    strain_read<T>(sh, Hp, Hc, iv, x, jfx, 2, err, Rp2, Rc2);
-    const float tau = (float)(j - sh.jc) * TAU_UNIT;
-#pragma unroll 1
-    for (int l = 0; l < 6; ++l) {
-        ff ep, ec;
-        strain_read<T>(sh, Hp, Hc, iv, x, jfx, 3 + l, err, ep, ec);
-        const int r = l < 3 ? l : (l == 3 ? 0 : (l == 4 ? 2 : 1));   // receiving spacecraft
-        const ff rp = r == 0 ? Rp0 : (r == 1 ? Rp1 : Rp2);
-        const ff rc = r == 0 ? Rc0 : (r == 1 ? Rc1 : Rc2);
-        store(l, ff_add(ff_mul(geom_at(sh, l, tau), ff_sub(ep, rp)), ff_mul(geom_at(sh, 6 + l, tau), ff_sub(ec, rc))));
-    }
-}
-
-// exact-weight read of a link series (used where the integer index differs from the tile's
-// reference): kept out of line, it is rare
-template <int T>
-__device__ __noinline__ ff link_read_exact(const CompSeries S, int m, float ehi, float elo)
-{
-    constexpr int NU = T >= 4 ? T - 3 : 1;
-    float U[NU];
-    if constexpr (T >= 4) comp_weights<T>(ehi, U);
-    return comp_value<T>(S, m, ehi, elo, U);
-}
-
-// X, Y, Z of one output sample: for each channel the two Michelson chains, each a running
-// fixed-point delay over the chain's links; every delayed read uses the tile-reference expansion
-// of its correction weights unless its integer index differs from the reference.
-template <int T>
-__device__ __forceinline__ void tdi_sample_mx(const FwdParams &P, const MxShared &sh, float *ybase, int ystride, int nl,
-                                              const float *tw, long long L0, long long L1, long long L2, long long L3,
-                                              long long L4, long long L5, double *o, int64_t N, double us)
-{
-    constexpr int NU = T >= 4 ? T - 3 : 1;
-    constexpr int h = (T - 2) / 2;
-    const long long nlfx = (long long)nl << FX_BITS;
-#pragma unroll 1
-    for (int ch = 0; ch < 3; ++ch) {
-        ff acc = {0.0f, 0.0f};
-#pragma unroll 1
-        for (int c = 0; c < 2; ++c) {
-            const int l0 = c_tdimx.link[ch][c][0];
-            ff part = {ybase[(6 * l0 + 0) * ystride + nl], ybase[(6 * l0 + 1) * ystride + nl]};
-            long long D = 0;
-#pragma unroll 1
-            for (int q = 1; q <= P.q_terms; ++q) {
-                D += pick(c_tdimx.pair[ch][c][q], L0, L1, L2, L3, L4, L5);
-                const int lk = c_tdimx.link[ch][c][q];
-                const int id = (ch * 2 + c) * 7 + (q - 1);
-                CompSeries S = series_at(ybase + 6 * lk * ystride, ystride);
-                Split s = split_fx(nlfx - D);
-                ff v;
-                if (s.m - h < 0 || s.m + h + 1 >= sh.ny) {
-                    atomicOr(P.err, ERR_WINDOW);
-                    v = {0.0f, 0.0f};
-                } else if (s.m - nl == sh.tfm[id]) {
-                    const float delta = (s.ehi - sh.tehi[id]) + (s.elo - sh.telo[id]);
-                    const float *w0 = tw + (size_t)id * 3 * NU;
-                    v = comp_value_taylor<T>(S, s.m, s.ehi, s.elo, w0, w0 + NU, delta);
-                } else {
-                    v = link_read_exact<T>(S, s.m, s.ehi, s.elo);
-                }
-                part = ff_add(part, v);
-            }
-            acc = c == 0 ? part : ff_sub(acc, part);
+    float eh[PB], el[PB];
+    int m0;
+    bool steady = true;
+    {
+        const PosPiece p = sh.pp[piece][rd];
+        const int r0 = j0 - sh.jc;
+        const float rf0 = (float)r0;
+        long long X = p.Xc + (long long)r0 * p.Vc - woff_fx;
+        int mk0 = 0;
+#pragma unroll
+        for (int k = 0; k < PB; ++k) {
+            const Split s = split_fx(X + piece_rem(p, rf0 + (float)k));
+            if (k == 0)
+                mk0 = s.m;
+            else if (k < kmax)
+                steady = steady && (s.m == mk0 + k);
+            eh[k] = s.ehi;
+            el[k] = s.elo;
+            X += p.Vc;
         }
-        o[ch * N] = ff_to_double(acc) * us;
+        m0 = mk0;
+    }
+    if (!steady) {
+        proj_item_exact<T>(smf, sh, rd, j0, kmax, wlen, woff_fx, err);
+        return;
+    }
+    if (m0 - h < 0 || m0 + kmax + h >= wlen) {
+        atomicOr(err, ERR_WINDOW);
+        for (int k = 0; k < kmax; ++k) {
+            store_read(smf, rd, 0, j0 + k, {0.0f, 0.0f});
+            store_read(smf, rd, 1, j0 + k, {0.0f, 0.0f});
+        }
+        return;
+    }
+    // 8-phase offsets of the window start x = m0 - h: element a sits at o[a % 8] + a / 8
+    const int x = m0 - h;
+    int o[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) o[r] = phw(x + r);
+    const float eref = kmax == PB ? eh[PB / 2] : eh[0];
+    float U0[NU], U1[NU];
+    if constexpr (T >= 4) comp_weights_d<T>(eref, U0, U1);
+#pragma unroll
+    for (int pol = 0; pol < 2; ++pol) {
+        float E[NE];
+        if constexpr (T >= 4) {
+#pragma unroll
+            for (int a = 0; a < NE; ++a) E[a] = smf[warr(pol, A_E) + o[a & 7] + (a >> 3)];
+        }
+#pragma unroll
+        for (int k = 0; k < PB; ++k) {
+            float C = 0.0f;
+            if constexpr (T >= 4) {
+                float c0 = 0.0f, c1 = 0.0f;
+#pragma unroll
+                for (int a = 0; a < NU; ++a) {
+                    c0 = fmaf(U0[a], E[k + a], c0);
+                    c1 = fmaf(U1[a], E[k + a], c1);
+                }
+                C = fmaf((eh[k] - eref) + el[k], c1, c0);
+            }
+            const ff v = strain_anchor<T>(smf, pol, o[(h + k) & 7] + ((h + k) >> 3), eh[k], el[k], C);
+            if (k < kmax) store_read(smf, rd, pol, j0 + k, v);
+        }
     }
 }
 
-// ---------------------------------------------------------------- kernels
-// Shared memory (floats): [strain tables 14 W][link tables 36 Y (also the FP64 staging
-// buffer, 4 W floats)][TDI correction weights 3*42*(T-3)].
-__host__ __device__ inline void mx_layout(const FwdParams &P, int T, size_t *r2, size_t *r3, size_t *total)
+// ---------------------------------------------------------------- TDI reads
+// sgn * (s + eps d) added to the float-float accumulator (hi, lo) exactly up to the low parts;
+// sgn * (eps (eps - 1) a - C) added to the FP32 accumulator sm (T >= 4), with eps = eh + el and
+// eps (eps - 1) = q0 + el g (q0 = eh (eh - 1), g = 2 eh - 1).
+template <int SG, int T>
+__device__ __forceinline__ void acc_term(float &hi, float &lo, float &sm, float shi, float slo, float dhi, float dlo,
+                                         float a, float eh, float el, float q0, float g, float C)
 {
-    const size_t W = (size_t)P.wmax, Y = (size_t)P.ymax;
-    size_t a = 14 * W;
-    size_t b = 36 * Y > 4 * W ? 36 * Y : 4 * W;
-    if (12 * Y > a) a = 12 * Y;  // TDI-only launches stage FP64 link series in region 1
-    size_t c = 3 * NTERM * (size_t)(T >= 4 ? T - 3 : 1);
-    *r2 = a;
-    *r3 = a + b;
-    *total = a + b + c;
+    const float p = eh * dhi;
+    const float pe = fmaf(eh, dhi, -p);
+    const ff t1 = two_sum(hi, SG > 0 ? shi : -shi);
+    const ff t2 = two_sum(t1.hi, SG > 0 ? p : -p);
+    hi = t2.hi;
+    const float l = slo + (pe + fmaf(eh, dlo, el * dhi));
+    lo += (SG > 0 ? l : -l) + (t1.lo + t2.lo);
+    if constexpr (T >= 4) {  // degree 1: the linear anchor alone
+        const float c = fmaf(fmaf(el, g, q0), a, -C);
+        sm += SG > 0 ? c : -c;
+    }
 }
 
-template <int T, int KIND>
-__global__ void __launch_bounds__(256, 2) k_mixed(FwdParams P)
+// one delayed read of link lk with exact weights (the rare reads off the tile reference);
+// an out-of-window stencil reads 0 and records ERR_WINDOW
+template <int T>
+__device__ __noinline__ void tdi_read_exact(const float *smf, int lk, int m, float eh, float el, int ny, int *err,
+                                            float *out)
 {
-    extern __shared__ float smf[];
+    constexpr int h = (T - 2) / 2;
+    if (m - h < 0 || m + h + 1 >= ny) {
+        atomicOr(err, ERR_WINDOW);
+        for (int i = 0; i < 6; ++i) out[i] = 0.0f;
+        return;
+    }
+    const int yb = ybase(lk);
+    float C = 0.0f;
+    if constexpr (T >= 4) {
+        float U[T - 3];
+        comp_weights<T>(eh, U);
+#pragma unroll
+        for (int a = 0; a < T - 3; ++a) C = fmaf(U[a], smf[yb + A_E * MX_AY + phy(m - h + a)], C);
+    }
+    const int ai = phy(m);
+    out[0] = smf[yb + A_SHI * MX_AY + ai];
+    out[1] = smf[yb + A_SLO * MX_AY + ai];
+    out[2] = smf[yb + A_DHI * MX_AY + ai];
+    out[3] = smf[yb + A_DLO * MX_AY + ai];
+    out[4] = smf[yb + A_A * MX_AY + ai];
+    out[5] = C;
+}
+
+// Chain c (sign SG) of channel ch for the outputs of item b (i0 = 4 b; nl = output index in
+// the span).  The chained delay of the item's first output is carried in 64-bit fixed point
+// and split once per term; the other outputs differ from it by the exact FP32 increments
+// dk, so output k reads at index m0 + k with fraction eh + (el - dk 2^-44) while that stays
+// in [0, 1).
+template <int T, int SG>
+__device__ __forceinline__ void tdi_chain(const FwdParams &P, const MxShared &sh, const float *smf,
+                                          const long long *Lblk, const float *dLf, int ch, int b, int kmax,
+                                          float *hi, float *lo, float *sm)
+{
+    constexpr int c = SG > 0 ? 0 : 1;
+    constexpr int h = (T - 2) / 2;
+    constexpr int NU = T >= 4 ? T - 3 : 1;
+    constexpr int NE = NU + TB - 1;
+    constexpr int NUP = mx_nup(T);
+    const int ny = sh.ny;
+    const int i0 = TB * b;
+    const int nl0 = i0 + P.HL;
+    {
+        const int yb = ybase(c_tdimx.link[ch][c][0]);
+#pragma unroll
+        for (int k = 0; k < TB; ++k) {
+            const int ai = phy(nl0 + k);
+            const float shi = smf[yb + A_SHI * MX_AY + ai], slo = smf[yb + A_SLO * MX_AY + ai];
+            const ff t = two_sum(hi[k], SG > 0 ? shi : -shi);
+            hi[k] = t.hi;
+            lo[k] += (SG > 0 ? slo : -slo) + t.lo;
+        }
+    }
+    long long D0 = 0;
+    float dk[TB];
+#pragma unroll
+    for (int k = 0; k < TB; ++k) dk[k] = 0.0f;
+#pragma unroll 1
+    for (int q = 1; q <= P.q_terms; ++q) {
+        const int pl = c_tdimx.pair[ch][c][q];
+        const int lk = c_tdimx.link[ch][c][q];
+        const int id = (ch * 2 + c) * 7 + q - 1;
+        D0 += Lblk[pl * LB + b];
+        const float4 dv = reinterpret_cast<const float4 *>(dLf + pl * LT)[b];
+        dk[1] += dv.y;
+        dk[2] += dv.z;
+        dk[3] += dv.w;
+        const Split s0 = split_fx(((long long)nl0 << FX_BITS) - D0);
+        const int m0 = s0.m;
+        const float eh = s0.ehi;
+        float el[TB];
+        el[0] = s0.elo;
+#pragma unroll
+        for (int k = 1; k < TB; ++k) el[k] = fmaf(-dk[k], 0x1p-44f, s0.elo);
+        bool fast = (m0 - nl0 == sh.tfm[id]) && (m0 - h >= 0) && (m0 + kmax + h < ny);
+#pragma unroll
+        for (int k = 1; k < TB; ++k) fast = fast && (k >= kmax || (eh + el[k] >= 0.0f && eh + el[k] < 1.0f));
+        const int yb = ybase(lk);
+        const float q0 = eh * (eh - 1.0f), g = 2.0f * eh - 1.0f;
+        if (fast) {
+            const int x = m0 - h;
+            int o[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) o[r] = phy(x + r);
+            float C[TB];
+#pragma unroll
+            for (int k = 0; k < TB; ++k) C[k] = 0.0f;
+            if constexpr (T >= 4) {
+                const float dref = eh - sh.tehi[id];
+                unsigned long long ee[NE];  // (e, e) pairs of the window
+#pragma unroll
+                for (int a = 0; a < NE; ++a) {
+                    const float v = smf[yb + A_E * MX_AY + o[a & 7] + (a >> 3)];
+                    ee[a] = f2pack(v, v);
+                }
+                unsigned long long acc[TB];  // (sum U e, sum dU e)
+#pragma unroll
+                for (int k = 0; k < TB; ++k) acc[k] = 0ull;
+                const ulonglong2 *w = reinterpret_cast<const ulonglong2 *>(smf + OFF_TW) + id * (NUP / 2);
+#pragma unroll
+                for (int a2 = 0; a2 < NUP / 2; ++a2) {
+                    const ulonglong2 u = w[a2];  // (U, dU) at taps 2 a2 and 2 a2 + 1
+#pragma unroll
+                    for (int k = 0; k < TB; ++k) {
+                        acc[k] = ffma2(u.x, ee[k + 2 * a2], acc[k]);
+                        if (2 * a2 + 1 < NU) acc[k] = ffma2(u.y, ee[k + 2 * a2 + 1], acc[k]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < TB; ++k) {
+                    float c0, c1;
+                    f2unpack(acc[k], c0, c1);
+                    C[k] = fmaf(dref + el[k], c1, c0);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < TB; ++k) {
+                const int ai = o[(h + k) & 7] + ((h + k) >> 3);
+                acc_term<SG, T>(hi[k], lo[k], sm[k], smf[yb + A_SHI * MX_AY + ai], smf[yb + A_SLO * MX_AY + ai],
+                                smf[yb + A_DHI * MX_AY + ai], smf[yb + A_DLO * MX_AY + ai],
+                                smf[yb + A_A * MX_AY + ai], eh, el[k], q0, g, C[k]);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < TB; ++k) {
+                if (k < kmax) {
+                    const Split sk = split_fx(((long long)(nl0 + k) << FX_BITS) - (D0 + (long long)dk[k]));
+                    float r[6];
+                    tdi_read_exact<T>(smf, lk, sk.m, sk.ehi, sk.elo, ny, P.err, r);
+                    acc_term<SG, T>(hi[k], lo[k], sm[k], r[0], r[1], r[2], r[3], r[4], sk.ehi, sk.elo,
+                                    sk.ehi * (sk.ehi - 1.0f), 2.0f * sk.ehi - 1.0f, r[5]);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- kernel
+template <int T, int KIND>
+__global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdParams P)
+{
+    extern __shared__ __align__(16) float smf[];
     __shared__ MxShared sh;
-    size_t r2, r3, total;
-    mx_layout(P, T, &r2, &r3, &total);
-    float *R1 = smf, *R2 = smf + r2, *tw = smf + r3;
-    const int W = P.wmax, Y = P.ymax;
-    CompSeries Hp = series_at(R1, W, true), Hc = series_at(R1 + 7 * W, W, true);
+    constexpr int h = (T - 2) / 2;
     const int64_t tot = P.total_tiles >= 0 ? P.total_tiles : P.src.tile_off[P.src.S];
+    if (threadIdx.x == 0) sh.s_hint = 0;
     for (int64_t g = blockIdx.x; g < tot; g += gridDim.x) {
         if (threadIdx.x == 0) {
-            sh.ti = tile_info(P, g, KIND == KIND_PROJECT ? 6 : 3);
-            sh.sk = make_sky(sh.ti.sky);
+            mx_tile(P, g, KIND == KIND_PROJECT ? 6 : 3, sh.s_hint, sh.ti, sh.sk);
             if (!sh.ti.ok) atomicOr(P.err, ERR_OFFSETS);
             const int hl = KIND == KIND_PROJECT ? 0 : P.HL, hr = KIND == KIND_PROJECT ? 0 : P.HR;
             sh.k_lo = sh.ti.n0 - hl;
             sh.ny = (int)sh.ti.nb + hl + hr;
             sh.u0 = (P.t0 - sh.ti.t0h) / P.dt;
-            const int h = (T - 2) / 2;
-            sh.w_lo = sh.k_lo + (int64_t)floor(sh.u0) - P.sig_b - P.lproj_b - h - 2;
-            sh.wlen = sh.ny + 2 * P.sig_b + P.lproj_b + T + 4;
             sh.maxbits = 0ull;
+            sh.wlo = INT_MAX;
+            sh.whi = INT_MIN;
+            if (sh.ny > MX_YCAP) {
+                atomicOr(P.err, ERR_WINDOW);
+                sh.ti.ok = 0;
+            }
         }
         __syncthreads();
         if (!sh.ti.ok || sh.ti.nb <= 0) {
@@ -487,97 +815,143 @@ __global__ void __launch_bounds__(256, 2) k_mixed(FwdParams P)
             continue;
         }
         const int ny = sh.ny, nb = (int)sh.ti.nb;
-        // ---- phase 1: stage raw inputs and their max; per-tile cubics and geometry nodes
+        // ---- setup
+        setup_tile<KIND>(P, sh);
+        __syncthreads();
+        // ---- stage raw inputs and their maximum; geometry fit; TDI references
+        int wlen = 0;
+        long long woff_fx = 0;
         if (KIND != KIND_TDI) {
-            double *tmp = reinterpret_cast<double *>(R2);
-            double mx = 0.0;
-            for (int j = threadIdx.x; j < sh.wlen; j += blockDim.x) {
-                int64_t i = sh.w_lo + j;
-                bool in = i >= 0 && i < sh.ti.nh;
-                double a = in ? __ldg(sh.ti.hp + i) : 0.0, b = in ? __ldg(sh.ti.hc + i) : 0.0;
+            const long long span = (long long)sh.whi - (long long)sh.wlo + T + 4;
+            wlen = span > 0 && span <= MX_WCAP ? (int)span : MX_WCAP;
+            if (!(span > 0 && span <= MX_WCAP) && threadIdx.x == 0) atomicOr(P.err, ERR_WINDOW);
+            const int woff = sh.wlo - h - 2;
+            woff_fx = (long long)woff << FX_BITS;
+            double *tmp = reinterpret_cast<double *>(smf + OFF_Y);
+            unsigned long long mx = 0ull;
+            for (int j = threadIdx.x; j < wlen; j += blockDim.x) {
+                const int64_t i = sh.k_lo + woff + j;
+                const bool in = i >= 0 && i < sh.ti.nh;
+                const double a = in ? __ldg(sh.ti.hp + i) : 0.0, b = in ? __ldg(sh.ti.hc + i) : 0.0;
                 tmp[j] = a;
-                tmp[W + j] = b;
-                mx = fmax(mx, fmax(fabs(a), fabs(b)));
+                tmp[MX_WCAP + j] = b;
+                mx = max(mx, max(abs_bits(a), abs_bits(b)));
             }
             block_absmax(&sh.maxbits, mx);
-            setup_projection(P, sh);
+            fit_geometry(P, sh);
         } else {
-            double *tmp = reinterpret_cast<double *>(R1);
-            double mx = 0.0;
+            double *tmp = reinterpret_cast<double *>(smf + OFF_W);
+            unsigned long long mx = 0ull;
             for (int l = 0; l < 6; ++l)
                 for (int j = threadIdx.x; j < ny; j += blockDim.x) {
-                    int64_t k = sh.k_lo + j;
-                    double v = (k >= 0 && k < sh.ti.N) ? __ldg(sh.ti.yin + l * sh.ti.N + k) : 0.0;
-                    tmp[l * Y + j] = v;
-                    mx = fmax(mx, fabs(v));
+                    const int64_t k = sh.k_lo + j;
+                    const double v = (k >= 0 && k < sh.ti.N) ? __ldg(sh.ti.yin + l * sh.ti.N + k) : 0.0;
+                    tmp[l * MX_YCAP + j] = v;
+                    mx = max(mx, abs_bits(v));
                 }
             block_absmax(&sh.maxbits, mx);
         }
-        if (KIND != KIND_PROJECT) setup_tdi(P, sh, sh.ti.n0, nb);
+        if (KIND != KIND_PROJECT) tdi_refs<T>(P, sh, smf + OFF_TW);
         __syncthreads();
-        // ---- phase 2: scale, geometry fits, TDI reference weights
-        if (threadIdx.x == 0) set_scale(sh);
-        if (KIND != KIND_TDI) fit_geometry(P, sh);
-        if (KIND != KIND_PROJECT) setup_tdi_refs<T>(P, sh, nb, tw);
-        __syncthreads();
-        // ---- phase 3: scaled float-float values
+        // ---- scaled float-float values
+        double scale, unscale;
+        tile_scale(sh.maxbits, scale, unscale);
         if (KIND != KIND_TDI) {
-            const double *tmp = reinterpret_cast<const double *>(R2);
-            for (int j = threadIdx.x; j < sh.wlen; j += blockDim.x) {
-                ff a = ff_from_double(tmp[j] * sh.scale), b = ff_from_double(tmp[W + j] * sh.scale);
-                Hp.shi[j] = a.hi; Hp.slo[j] = a.lo;
-                Hc.shi[j] = b.hi; Hc.slo[j] = b.lo;
+            const double *tmp = reinterpret_cast<const double *>(smf + OFF_Y);
+            for (int j = threadIdx.x; j < wlen; j += blockDim.x) {
+                const ff a = ff_from_double(tmp[j] * scale), b = ff_from_double(tmp[MX_WCAP + j] * scale);
+                const int p = phw(j);
+                smf[warr(0, A_SHI) + p] = a.hi;
+                smf[warr(0, A_SLO) + p] = a.lo;
+                smf[warr(1, A_SHI) + p] = b.hi;
+                smf[warr(1, A_SLO) + p] = b.lo;
             }
         } else {
-            const double *tmp = reinterpret_cast<const double *>(R1);
+            const double *tmp = reinterpret_cast<const double *>(smf + OFF_W);
             for (int l = 0; l < 6; ++l)
                 for (int j = threadIdx.x; j < ny; j += blockDim.x) {
-                    ff v = ff_from_double(tmp[l * Y + j] * sh.scale);
-                    R2[(6 * l + 0) * Y + j] = v.hi;
-                    R2[(6 * l + 1) * Y + j] = v.lo;
+                    const ff v = ff_from_double(tmp[l * MX_YCAP + j] * scale);
+                    smf[ybase(l) + A_SHI * MX_AY + phy(j)] = v.hi;
+                    smf[ybase(l) + A_SLO * MX_AY + phy(j)] = v.lo;
                 }
         }
-        if (KIND != KIND_PROJECT) finish_tdi_refs<T>(P, tw);
         __syncthreads();
-        // ---- phase 4/5: strain difference tables, link series
+        long long *Lblk = reinterpret_cast<long long *>(smf + OFF_W);
+        float *dLf = smf + OFF_W + 2 * 6 * LB;
         if (KIND != KIND_TDI) {
-            build_tables_ff(sh.wlen, Hp);
-            build_tables_ff(sh.wlen, Hc);
+            // ---- strain difference tables
+            build_tables<true, RLW>(smf, warr(0, A_SHI), MX_AW, 7 * MX_AW, 2, wlen);
             __syncthreads();
+            // ---- projection reads
+            const int nblk = (ny + PB - 1) / PB;
+            for (int it = threadIdx.x; it < 9 * nblk; it += blockDim.x)
+                proj_item<T>(smf, sh, it / nblk, it % nblk, ny, wlen, woff_fx, P.err);
+            __syncthreads();
+            // ---- link series (in place over the staged reads) and the tile's link delays
             for (int j = threadIdx.x; j < ny; j += blockDim.x) {
+                const int ai = phy(j);
+                ff rp[3], rc[3];
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    rp[r] = {smf[OFF_Y + (4 * r + 0) * MX_AY + ai], smf[OFF_Y + (4 * r + 1) * MX_AY + ai]};
+                    rc[r] = {smf[OFF_Y + (4 * r + 2) * MX_AY + ai], smf[OFF_Y + (4 * r + 3) * MX_AY + ai]};
+                }
+                const float tau = (float)(j - sh.jc) * TAU_UNIT;
+                ff y[6];
+#pragma unroll
+                for (int l = 0; l < 6; ++l) {
+                    const int rd = 3 + l;
+                    const ff ep = {smf[OFF_Y + (4 * rd + 0) * MX_AY + ai], smf[OFF_Y + (4 * rd + 1) * MX_AY + ai]};
+                    const ff ec = {smf[OFF_Y + (4 * rd + 2) * MX_AY + ai], smf[OFF_Y + (4 * rd + 3) * MX_AY + ai]};
+                    const int r = l < 3 ? l : (l == 3 ? 0 : (l == 4 ? 2 : 1));  // receiving spacecraft
+                    y[l] = ff_add(ff_mul(geom_at(sh, l, tau), ff_sub(ep, rp[r])),
+                                  ff_mul(geom_at(sh, 6 + l, tau), ff_sub(ec, rc[r])));
+                }
                 const int64_t k = sh.k_lo + j;
-                const bool in = k >= 0 && k < sh.ti.N;
                 if (KIND == KIND_PROJECT) {
                     double *o = sh.ti.out;
                     const int64_t N = sh.ti.N;
-                    const double us = sh.unscale;
-                    project_sample_mx<T>(sh, Hp, Hc, j, P.err,
-                                         [&](int l, ff v) { o[l * N + k] = ff_to_double(v) * us; });
-                } else if (in) {
-                    project_sample_mx<T>(sh, Hp, Hc, j, P.err, [&](int l, ff v) {
-                        R2[(6 * l + 0) * Y + j] = v.hi;
-                        R2[(6 * l + 1) * Y + j] = v.lo;
-                    });
+#pragma unroll
+                    for (int l = 0; l < 6; ++l) o[l * N + k] = ff_to_double(y[l]) * unscale;
                 } else {
+                    const bool in = k >= 0 && k < sh.ti.N;
 #pragma unroll
                     for (int l = 0; l < 6; ++l) {
-                        R2[(6 * l + 0) * Y + j] = 0.0f;
-                        R2[(6 * l + 1) * Y + j] = 0.0f;
+                        smf[ybase(l) + A_SHI * MX_AY + ai] = in ? y[l].hi : 0.0f;
+                        smf[ybase(l) + A_SLO * MX_AY + ai] = in ? y[l].lo : 0.0f;
                     }
                 }
             }
         }
-        // ---- phase 6/7: link difference tables, X, Y, Z
         if (KIND != KIND_PROJECT) {
+            // link delays of the outputs: at each item's first output (fixed point) and the
+            // increments to the item's other outputs (rows padded to whole items)
+            const int nb4 = (nb + TB - 1) & ~(TB - 1);
+            for (int idx = threadIdx.x; idx < 6 * nb4; idx += blockDim.x) {
+                const int l = idx / nb4, i = idx - l * nb4, i0 = i & ~(TB - 1);
+                const long long Li = piece_at(sh.dp[i < sh.jswt ? 0 : 1][l], i - sh.ic);
+                const long long L0 = piece_at(sh.dp[i0 < sh.jswt ? 0 : 1][l], i0 - sh.ic);
+                dLf[l * LT + i] = (float)(Li - L0);
+                if (i == i0) Lblk[l * LB + i / TB] = Li;
+            }
             __syncthreads();
-            for (int l = 0; l < 6; ++l) build_tables_ff(ny, series_at(R2 + 6 * l * Y, Y));
+            // ---- link difference tables
+            build_tables<false, RLY>(smf, ybase(0), MX_AY, 6 * MX_AY, 6, ny);
             __syncthreads();
-            for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-                const int64_t n = sh.ti.n0 + i;
-                const int nl = (int)(n - sh.k_lo);
-                long long L0, L1, L2, L3, L4, L5;
-                tdi_delays_fx(sh, i, L0, L1, L2, L3, L4, L5);
-                tdi_sample_mx<T>(P, sh, R2, Y, nl, tw, L0, L1, L2, L3, L4, L5, sh.ti.out + n, sh.ti.N, sh.unscale);
+            // ---- X, Y, Z
+            const int nbb = (nb + TB - 1) / TB;
+            for (int it = threadIdx.x; it < 3 * nbb; it += blockDim.x) {
+                const int ch = it / nbb, b = it - ch * nbb, i0 = TB * b;
+                const int kmax = min(TB, nb - i0);
+                float hi[TB], lo[TB], sm[TB];
+#pragma unroll
+                for (int k = 0; k < TB; ++k) hi[k] = lo[k] = sm[k] = 0.0f;
+                tdi_chain<T, 1>(P, sh, smf, Lblk, dLf, ch, b, kmax, hi, lo, sm);
+                tdi_chain<T, -1>(P, sh, smf, Lblk, dLf, ch, b, kmax, hi, lo, sm);
+                double *o = sh.ti.out + ch * sh.ti.N + sh.ti.n0 + i0;
+#pragma unroll
+                for (int k = 0; k < TB; ++k)
+                    if (k < kmax) o[k] = ((double)hi[k] + (double)(lo[k] + sm[k])) * unscale;
             }
         }
         __syncthreads();
@@ -610,9 +984,8 @@ static void *kernel_for_mx(int kind, int order)
 int smem_fwdmx(int kind, int order, const FwdParams &P, size_t *smem)
 {
     (void)kind;
-    size_t r2, r3, total;
-    mx_layout(P, order + 1, &r2, &r3, &total);
-    *smem = total * sizeof(float);
+    (void)P;
+    *smem = (size_t)mx_smem_floats(order + 1) * sizeof(float);
     return 0;
 }
 

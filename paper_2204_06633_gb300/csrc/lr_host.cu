@@ -183,11 +183,12 @@ bool light_time(const lr_orbit *o, int l, double t, double *out)
 // Inverse of the Vandermonde matrix V_ik = c_i^k of the four Chebyshev nodes
 // c_i = cos((2i+1) pi / 8): row k maps node values to the coefficient of s^k of the cubic
 // through them (Gauss-Jordan elimination with partial pivoting).
-void chebyshev_inverse(double out[4][4])
+void chebyshev_inverse(double out[4][4], double node[4])
 {
     double a[4][8];
     for (int i = 0; i < 4; ++i) {
         double c = std::cos((2.0 * i + 1.0) * 3.14159265358979323846 / 8.0), pw = 1.0;
+        node[i] = c;
         for (int k = 0; k < 4; ++k) {
             a[i][k] = pw;
             pw *= c;
@@ -450,11 +451,6 @@ LR_API int lr_plan_create(lr_ctx *ctx, const lr_plan_desc *d, lr_plan **out)
     }
     P.HL = (int)std::ceil(chain) + p->h + 2;
     P.HR = p->h + 2;
-    if (P.tile == 0) {
-        // mixed: the tile plus its link halo fills exactly one pass of the CTA's threads
-        P.tile = d->precision == LR_MIXED ? std::max(32, lr::MIXED_THREADS - P.HL - P.HR)
-                                          : lr::default_tile(d->precision, d->order);
-    }
     double sig = d->proj_orbit->max_r_over_c / d->dt;
     double lp = d->proj_orbit->max_delay / d->dt;
     if (sig > 1e6 || lp > 1e6) {
@@ -463,6 +459,17 @@ LR_API int lr_plan_create(lr_ctx *ctx, const lr_plan_desc *d, lr_plan **out)
     }
     P.sig_b = (int)std::ceil(sig) + 1;
     P.lproj_b = (int)std::ceil(lp) + 1;
+    if (d->precision == LR_MIXED) {
+        // mixed tiles are staged in fixed shared-memory arrays: the largest tile that fits
+        const int tmax = lr::mx_max_tile(P.HL, P.HR, P.lproj_b, p->T);
+        if (tmax < 4 || (P.tile != 0 && P.tile > tmax)) {
+            delete p;
+            return LR_ERR_RANGE;
+        }
+        if (P.tile == 0) P.tile = tmax;
+    } else if (P.tile == 0) {
+        P.tile = lr::default_tile(d->precision, d->order);
+    }
     P.ymax = P.tile + P.HL + P.HR;
     P.wmax = P.ymax + 2 * P.sig_b + P.lproj_b + p->T + 4;
     if (d->precision == LR_MIXED) {
@@ -477,7 +484,7 @@ LR_API int lr_plan_create(lr_ctx *ctx, const lr_plan_desc *d, lr_plan **out)
             return LR_ERR_RANGE;
         }
     }
-    chebyshev_inverse(P.cheb);
+    chebyshev_inverse(P.cheb, P.cheb_node);
     cudaError_t e = lr::dev_malloc((void **)&p->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
     if (e != cudaSuccess) {
@@ -610,6 +617,7 @@ LR_API int lr_project(lr_plan *plan, const double *hp, const double *hc, int64_t
     P.src.nh1 = n_h;
     P.src.t0h1 = t0_h;
     P.src.sky1 = sky;
+    P.src.skyc1 = lr::make_sky(sky);
     P.hp = hp;
     P.hc = hc;
     P.out = y;
@@ -640,6 +648,7 @@ LR_API int lr_response(lr_plan *plan, const double *hp, const double *hc, int64_
     P.src.nh1 = n_h;
     P.src.t0h1 = t0_h;
     P.src.sky1 = sky;
+    P.src.skyc1 = lr::make_sky(sky);
     P.hp = hp;
     P.hc = hc;
     P.out = xyz;
@@ -653,17 +662,13 @@ LR_API int lr_response_batched(lr_plan *plan, int64_t S, const int64_t *h_off, c
     if (!plan || !h_off || !out_off || !t0_h || !sky || !hp || !hc || !xyz) return LR_ERR_INVALID_ARG;
     if (S < 1) return LR_ERR_INVALID_ARG;
     if (S > (int64_t)1 << 24) return LR_ERR_RANGE;
-    if (S + 1 > plan->tile_cap) {
-        if (plan->d_tile_off) cudaFree(plan->d_tile_off);
-        plan->d_tile_off = nullptr;
-        plan->tile_cap = 0;
-        cudaError_t e = lr::dev_malloc((void **)&plan->d_tile_off, sizeof(int64_t) * (size_t)(S + 1));
-        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LR_ERR_OOM : cuda_fail(plan->ctx, e);
-        plan->tile_cap = S + 1;
-    }
+    int st = lr::plan_reserve_batch(plan, S);
+    if (st) return st;
     lr::FwdParams P = plan->base;
-    int e = lr::launch_tile_offsets(out_off, S, P.tile, plan->d_tile_off, P.err, stream);
+    lr::SkyConst *skyc = plan->desc.precision == LR_MIXED ? lr::plan_sky_table(plan) : nullptr;
+    int e = lr::launch_batch_tables(out_off, sky, S, P.tile, plan->d_tile_off, skyc, P.err, stream);
     if (e) return check_launch(plan->ctx, e);
+    P.src.skyc = skyc;
     P.src.h_off = h_off;
     P.src.out_off = out_off;
     P.src.t0h = t0_h;
@@ -785,7 +790,8 @@ int plan_set_tile(lr_plan *plan, int tile)
     FwdParams &P = plan->base;
     const int ymax = tile + P.HL + P.HR;
     if (plan->desc.precision == LR_MIXED &&
-        ((double)ymax * plan->desc.dt >= plan->desc.proj_orbit->dk || (double)tile * plan->desc.dt >= plan->desc.tdi_orbit->dk))
+        ((double)ymax * plan->desc.dt >= plan->desc.proj_orbit->dk || (double)tile * plan->desc.dt >= plan->desc.tdi_orbit->dk ||
+         tile > lr::mx_max_tile(P.HL, P.HR, P.lproj_b, plan->T)))
         return LR_ERR_RANGE;
     P.tile = tile;
     P.ymax = ymax;
@@ -800,10 +806,14 @@ int plan_reserve_batch(lr_plan *plan, int64_t S)
     if (plan->d_tile_off) cudaFree(plan->d_tile_off);
     plan->d_tile_off = nullptr;
     plan->tile_cap = 0;
-    cudaError_t e = lr::dev_malloc((void **)&plan->d_tile_off, sizeof(int64_t) * (size_t)(S + 1));
+    // one allocation: the tile table [S+1] followed by the sky frames [S+1]
+    const size_t bytes = (sizeof(int64_t) + sizeof(SkyConst)) * (size_t)(S + 1);
+    cudaError_t e = lr::dev_malloc((void **)&plan->d_tile_off, bytes);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LR_ERR_OOM : cuda_fail(plan->ctx, e);
     plan->tile_cap = S + 1;
     return LR_OK;
 }
+
+SkyConst *plan_sky_table(lr_plan *plan) { return reinterpret_cast<SkyConst *>(plan->d_tile_off + plan->tile_cap); }
 
 }  // namespace lr

@@ -1,5 +1,6 @@
 // Internal types shared by the host side of the library and its kernels.
 #pragma once
+#include <math.h>
 #include <stdint.h>
 
 #include "lisaresp.h"
@@ -32,6 +33,33 @@ struct TdiTab {
     signed char pair[3][2][CHAIN_TERMS];
 };
 
+// Sky frame of a source: k = -e_r, u = -e_phi, v = -e_theta of the SSB basis (Sec. "Reference
+// frames"); c2p, s2p rotate the antenna patterns by 2 psi.
+struct SkyConst {
+    double k[3], u[3], v[3];
+    double c2p, s2p;
+};
+
+__host__ __device__ inline SkyConst make_sky(const lr_sky &s)
+{
+    SkyConst c;
+    double sl, cl, sb, cb, s2, c2;
+#ifdef __CUDA_ARCH__
+    sincos(s.lam, &sl, &cl);
+    sincos(s.beta, &sb, &cb);
+    sincos(2.0 * s.psi, &s2, &c2);
+#else
+    sl = sin(s.lam); cl = cos(s.lam);
+    sb = sin(s.beta); cb = cos(s.beta);
+    s2 = sin(2.0 * s.psi); c2 = cos(2.0 * s.psi);
+#endif
+    c.k[0] = -cb * cl; c.k[1] = -cb * sl; c.k[2] = -sb;
+    c.u[0] = sl;       c.u[1] = -cl;      c.u[2] = 0.0;
+    c.v[0] = -sb * cl; c.v[1] = -sb * sl; c.v[2] = cb;
+    c.c2p = c2; c.s2p = s2;
+    return c;
+}
+
 // Per-call description of the sources processed by a launch.
 struct SrcArgs {
     // batched: device arrays (nullptr for a single-source launch)
@@ -40,11 +68,13 @@ struct SrcArgs {
     const double *t0h;
     const lr_sky *sky;
     const int64_t *tile_off;  // [S+1] prefix sums of tiles per source
+    const SkyConst *skyc;     // [S] sky frames (mixed launches; nullptr otherwise)
     int64_t S;
     // single source
     int64_t n1, nh1;
     double t0h1;
     lr_sky sky1;
+    SkyConst skyc1;
 };
 
 struct FwdParams {
@@ -66,6 +96,7 @@ struct FwdParams {
     int *err;               // device error word
     int64_t total_tiles;    // >= 0 single source; -1: read src.tile_off[S]
     double cheb[4][4];      // monomial coefficients of the cubic through 4 Chebyshev nodes on [-1, 1]
+    double cheb_node[4];    // the nodes cos((2 i + 1) pi / 8)
 };
 
 // error-word bits
@@ -85,5 +116,31 @@ int smem_fwdmx(int kind, int order, const FwdParams &P, size_t *smem);
 int max_blocks_fwdmx(int kind, int order, int threads, size_t smem, int *blocks);
 bool order_compiled_mx(int order);
 constexpr int MIXED_THREADS = 256;  // the mixed kernels' per-tile setup assigns work by thread index
+
+// Shared-memory geometry of the mixed kernels (compile time, so every array offset is an
+// immediate).  A staged series of up to n samples is stored in 8 phases: sample j at
+// (j mod 8) * RL + j / 8, with the row length RL four times an odd number; consecutive
+// samples, and every 4th or 8th sample across a warp, then fall in distinct banks.
+constexpr int MX_YCAP = 384;  // link span of a tile (outputs + TDI halo)
+constexpr int MX_WCAP = 466;  // strain window of a tile
+__host__ __device__ constexpr int mx_rl(int n) { return ((((n + 7) / 8 + 3) & ~3) / 4) % 2 ? (((n + 7) / 8 + 3) & ~3) : (((n + 7) / 8 + 3) & ~3) + 4; }
+constexpr int MX_AY = 8 * mx_rl(MX_YCAP);  // floats per link-span array
+constexpr int MX_AW = 8 * mx_rl(MX_WCAP);  // floats per strain-window array
+constexpr int MX_TDI_BLOCK = 4;            // consecutive outputs per TDI work item
+// correction-weight pairs (U, dU/deps) per TDI term, padded to a multiple of 2 pairs
+__host__ __device__ constexpr int mx_nup(int T) { return T >= 4 ? ((T - 3 + 1) & ~1) : 2; }
+__host__ __device__ constexpr int mx_smem_floats(int T) { return 14 * MX_AW + 36 * MX_AY + 42 * 2 * mx_nup(T); }
+// largest tile the mixed kernels stage: the link span within MX_YCAP, the strain window
+// (span + read spread 2 lproj_b + T + 6) within MX_WCAP, TDI items (3 channels x tile/4) in
+// one pass of the threads
+inline int mx_max_tile(int HL, int HR, int lproj_b, int T)
+{
+    int t = MX_YCAP - HL - HR;
+    int w = MX_WCAP - 2 * lproj_b - T - 6 - HL - HR;
+    if (w < t) t = w;
+    int one_pass = MX_TDI_BLOCK * (MIXED_THREADS / 3);
+    if (one_pass < t) t = one_pass;
+    return t & ~(MX_TDI_BLOCK - 1);
+}
 enum { KIND_PROJECT = 0, KIND_TDI = 1, KIND_FUSED = 2 };
 }  // namespace lr

@@ -75,4 +75,20 @@ int launch_tile_offsets(const int64_t *out_off, int64_t S, int tile, int64_t *ti
     return (int)cudaGetLastError();
 }
 
+__global__ void k_sky_consts(const lr_sky *__restrict__ sky, int64_t S, SkyConst *__restrict__ out)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x)
+        out[s] = make_sky(sky[s]);
+}
+
+int launch_batch_tables(const int64_t *out_off, const lr_sky *sky, int64_t S, int tile, int64_t *tile_off,
+                        SkyConst *skyc, int *err, void *stream)
+{
+    int e = launch_tile_offsets(out_off, S, tile, tile_off, err, stream);
+    if (e || !skyc) return e;
+    const int64_t blocks = (S + 255) / 256;
+    k_sky_consts<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, (cudaStream_t)stream>>>(sky, S, skyc);
+    return (int)cudaGetLastError();
+}
+
 }  // namespace lr

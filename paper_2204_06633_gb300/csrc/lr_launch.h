@@ -9,5 +9,8 @@ int default_tile(int precision, int order);
 // returns a cudaError_t value (0 = success)
 int launch_forward(int precision, int kind, int order, FwdParams &P, int threads, int sms, void *stream);
 int launch_tile_offsets(const int64_t *out_off, int64_t S, int tile, int64_t *tile_off, int *err, void *stream);
+// tile table and, when skyc is not null, the sky frame of every source
+int launch_batch_tables(const int64_t *out_off, const lr_sky *sky, int64_t S, int tile, int64_t *tile_off,
+                        SkyConst *skyc, int *err, void *stream);
 bool order_compiled(int order);
 }  // namespace lr

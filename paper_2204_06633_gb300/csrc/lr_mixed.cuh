@@ -110,11 +110,44 @@ __device__ __forceinline__ Split split_fx(long long X)
 }
 
 // ---------------------------------------------------------------- compensated weights
+// U[a] from r = w - q: left of the centre the triple running sums run from the left end; from
+// the centre on they run from the right end (r has three vanishing moments, so both give the
+// same U), which keeps each sum short and its rounding small.
+template <int T>
+__device__ __forceinline__ void triple_sums(const float *r, float *U)
+{
+    constexpr int h = (T - 2) / 2;
+    float s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+#pragma unroll
+    for (int a = 0; a < h; ++a) {
+        s1 += r[a];
+        s2 += s1;
+        s3 += s2;
+        if (a <= T - 4) U[a] = s3;
+    }
+    // right: U1_a = -sum_{b>a} r_b, U2_a = -sum_{a<b<=T-2} U1_b, U3_a = -sum_{a<b<=T-3} U2_b
+    float t1 = 0.0f, t2 = 0.0f, t3 = 0.0f;
+    float u1[T], u2[T];
+#pragma unroll
+    for (int a = T - 2; a >= h; --a) {
+        t1 -= r[a + 1];
+        u1[a] = t1;
+    }
+#pragma unroll
+    for (int a = T - 3; a >= h; --a) {
+        t2 -= u1[a + 1];
+        u2[a] = t2;
+    }
+#pragma unroll
+    for (int a = T - 4; a >= h; --a) {
+        t3 -= u2[a + 1];
+        U[a] = t3;
+    }
+}
+
 // U[0 .. T-4]: triple running sums of r = w - q, where w are the degree-(T-1) centered
 // Lagrange weights at eps (nodes a - h, h = (T-2)/2) and q the quadratic weights on the
-// nodes -1, 0, 1 (a = h-1, h, h+1).  Left of the centre the sums run from the left end;
-// from the centre on they run from the right end (r has three vanishing moments, so both
-// give the same U), which keeps each sum short and its rounding small.
+// nodes -1, 0, 1 (a = h-1, h, h+1).
 template <int T>
 __device__ __forceinline__ void comp_weights(float e, float *U)
 {
@@ -139,114 +172,46 @@ __device__ __forceinline__ void comp_weights(float e, float *U)
     w[h - 1] -= 0.5f * e * em1;
     w[h] -= (1.0f - e) * (1.0f + e);
     w[h + 1] -= 0.5f * e * (e + 1.0f);
-    // left: forward sums over a = 0 .. h-1
-    float s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-#pragma unroll
-    for (int a = 0; a < h; ++a) {
-        s1 += w[a];
-        s2 += s1;
-        s3 += s2;
-        if (a <= T - 4) U[a] = s3;
-    }
-    // right: U1_a = -sum_{b>a} r_b, U2_a = -sum_{a<b<=T-2} U1_b, U3_a = -sum_{a<b<=T-3} U2_b
-    float t1 = 0.0f, t2 = 0.0f, t3 = 0.0f;
-    float u1[T], u2[T];
-#pragma unroll
-    for (int a = T - 2; a >= h; --a) {
-        t1 -= w[a + 1];
-        u1[a] = t1;
-    }
-#pragma unroll
-    for (int a = T - 3; a >= h; --a) {
-        t2 -= u1[a + 1];
-        u2[a] = t2;
-    }
-#pragma unroll
-    for (int a = T - 4; a >= h; --a) {
-        t3 -= u2[a + 1];
-        U[a] = t3;
-    }
+    triple_sums<T>(w, U);
 }
 
-// Staged series in shared memory for compensated reads: value s (float-float), first
-// difference d = s_{j+1} - s_j (float-float), a = (s_{j+1} - 2 s_j + s_{j-1})/2 (FP32, plus its
-// low part alo for the strain, whose curvature term feeds two levels of cancellation) and
-// e = s_{j+3} - 3 s_{j+2} + 3 s_{j+1} - s_j (FP32).
-struct CompSeries {
-    float *shi, *slo, *dhi, *dlo, *a, *e, *alo;
-};
-
-// float-float s_m + eps d_m + eps (eps - 1) a_m - C; with FFQ the curvature product is formed
-// exactly (two_prod of eps_hi (eps_hi - 1), whose factors are exact in FP32) against the
-// float-float a_m, otherwise in FP32
-template <bool FFQ>
-__device__ __forceinline__ ff comp_finish(const CompSeries &S, int m, float ehi, float elo, float C)
-{
-    ff d = {S.dhi[m], S.dlo[m]};
-    float p = ehi * d.hi;
-    float pe = fmaf(ehi, d.hi, -p);
-    pe = fmaf(ehi, d.lo, pe);
-    pe = fmaf(elo, d.hi, pe);
-    ff r = ff_add({S.shi[m], S.slo[m]}, fast_two_sum(p, pe));
-    if constexpr (FFQ) {
-        const float em1 = ehi - 1.0f;
-        float q = ehi * em1;
-        float qe = fmaf(ehi, em1, -q);
-        qe = fmaf(elo, 2.0f * ehi - 1.0f, qe);
-        ff cq = ff_mul(fast_two_sum(q, qe), {S.a[m], S.alo[m]});
-        r = ff_add(r, cq);
-        r = ff_add_f(r, -C);
-    } else {
-        float small = fmaf(ehi * (ehi - 1.0f), S.a[m], -C);
-        r = ff_add_f(r, small);
-    }
-    return r;
-}
-
-// One compensated read at window index m (the anchor node) with fraction eps = ehi + elo
-// and correction weights U; returns the float-float value of the interpolant.
-template <int T, bool FFQ = false>
-__device__ __forceinline__ ff comp_value(const CompSeries &S, int m, float ehi, float elo, const float *U)
-{
-    constexpr int h = (T - 2) / 2;
-    float C = 0.0f;
-    if constexpr (T >= 4) {
-        const float *ep = S.e + (m - h);
-#pragma unroll
-        for (int a = 0; a <= T - 4; ++a) C = fmaf(U[a], ep[a], C);
-        return comp_finish<FFQ>(S, m, ehi, elo, C);
-    } else {
-        // degree 1: the interpolant is the linear anchor itself
-        ff d = {S.dhi[m], S.dlo[m]};
-        float p = ehi * d.hi;
-        float pe = fmaf(ehi, d.hi, -p);
-        pe = fmaf(ehi, d.lo, pe);
-        pe = fmaf(elo, d.hi, pe);
-        return ff_add({S.shi[m], S.slo[m]}, fast_two_sum(p, pe));
-    }
-}
-
-// The same read with the correction sum taken from a first-order expansion of U around a
-// reference fraction (U0 + delta U1); the anchor and the curvature term use the exact eps.
+// U and its exact derivative dU/deps at eps: the product rule carried through the prefix and
+// suffix products (each factor is linear in eps), the derivatives of the quadratic weights
+// subtracted, and the same triple sums applied to both (they are linear).
 template <int T>
-__device__ __forceinline__ ff comp_value_taylor(const CompSeries &S, int m, float ehi, float elo, const float *U0,
-                                                const float *U1, float delta)
+__device__ __forceinline__ void comp_weights_d(float e, float *U, float *U1)
 {
     constexpr int h = (T - 2) / 2;
-    if constexpr (T >= 4) {
-        float C = 0.0f, C1 = 0.0f;
-        const float *ep = S.e + (m - h);
+    float w[T], wd[T];
+    float L = 1.0f, Ld = 0.0f;
 #pragma unroll
-        for (int a = 0; a <= T - 4; ++a) {
-            float v = ep[a];
-            C = fmaf(U0[a], v, C);
-            C1 = fmaf(U1[a], v, C1);
-        }
-        C = fmaf(delta, C1, C);
-        return comp_finish<false>(S, m, ehi, elo, C);
-    } else {
-        return comp_value<T>(S, m, ehi, elo, U0);
+    for (int a = 0; a < T; ++a) {
+        w[a] = L;
+        wd[a] = Ld;
+        const float c1 = 1.0f / (float)(a + 1), c0 = (float)(h - a) / (float)(a + 1);
+        const float f = fmaf(e, c1, c0);
+        Ld = fmaf(Ld, f, L * c1);
+        L = L * f;
     }
+    float R = 1.0f, Rd = 0.0f;
+#pragma unroll
+    for (int a = T - 1; a >= 0; --a) {
+        const float sg = ((T - 1 - a) & 1) ? -1.0f : 1.0f;
+        wd[a] = sg * fmaf(wd[a], R, w[a] * Rd);
+        w[a] = sg * w[a] * R;
+        const float c1 = 1.0f / (float)(T - a), c0 = (float)(h - a) / (float)(T - a);
+        const float g = fmaf(e, c1, c0);
+        Rd = fmaf(Rd, g, R * c1);
+        R = R * g;
+    }
+    w[h - 1] -= 0.5f * e * (e - 1.0f);
+    w[h] -= (1.0f - e) * (1.0f + e);
+    w[h + 1] -= 0.5f * e * (e + 1.0f);
+    wd[h - 1] -= e - 0.5f;
+    wd[h] += 2.0f * e;
+    wd[h + 1] -= e + 0.5f;
+    triple_sums<T>(w, U);
+    triple_sums<T>(wd, U1);
 }
 
 }  // namespace lr

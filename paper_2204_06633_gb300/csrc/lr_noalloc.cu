@@ -20,16 +20,19 @@ namespace {
 constexpr int64_t kMaxSources = LR_NOALLOC_MAX_SOURCES;
 constexpr int kMaxDevices = 64;
 
-// the tile table: prefix sums of tiles per source, [S+1] entries, rewritten in full by every call
+// the tile table: prefix sums of tiles per source, [S+1] entries, and the sources' sky frames
+// [S] (mixed precision), rewritten in full by every call
 static __device__ __align__(256) int64_t g_tile_table[kMaxSources + 1];
+static __device__ __align__(256) lr::SkyConst g_sky_table[kMaxSources];
 
-// device address of g_tile_table on each device, looked up once per device
+// device addresses of g_tile_table and g_sky_table on each device, looked up once per device
 int64_t *g_table_addr[kMaxDevices];
+lr::SkyConst *g_sky_addr[kMaxDevices];
 std::mutex g_table_mutex;
 
-// In host code g_tile_table names a host-side stand-in, not device memory: its device address
-// comes from cudaGetSymbolAddress, taken once per device with that device current.
-int table_address(int device, int64_t **out)
+// In host code g_tile_table and g_sky_table name host-side stand-ins, not device memory: their
+// device addresses come from cudaGetSymbolAddress, taken once per device with that device current.
+int table_address(int device, int64_t **out, lr::SkyConst **sky_out)
 {
     if (device < 0 || device >= kMaxDevices) return (int)cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_table_mutex);
@@ -41,16 +44,19 @@ int table_address(int device, int64_t **out)
             e = cudaSetDevice(device);
             if (e != cudaSuccess) return (int)e;
         }
-        void *p = nullptr;
+        void *p = nullptr, *q = nullptr;
         e = cudaGetSymbolAddress(&p, g_tile_table);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress(&q, g_sky_table);
         if (prev != device) {
             cudaError_t e2 = cudaSetDevice(prev);
             if (e == cudaSuccess) e = e2;
         }
         if (e != cudaSuccess) return (int)e;
         g_table_addr[device] = static_cast<int64_t *>(p);
+        g_sky_addr[device] = static_cast<lr::SkyConst *>(q);
     }
     *out = g_table_addr[device];
+    *sky_out = g_sky_addr[device];
     return 0;
 }
 
@@ -67,12 +73,15 @@ extern "C" LR_API int lr_response_batched_noalloc(lr_plan *plan, int64_t S, cons
     int st = lr::plan_view(plan, &v);
     if (st) return st;
     int64_t *table = nullptr;
-    int e = table_address(v.device, &table);
+    lr::SkyConst *skytab = nullptr;
+    int e = table_address(v.device, &table, &skytab);
     if (e) return lr::plan_cuda_fail(plan, e);
     lr::FwdParams P = v.base;
-    // every entry of the table the launch reads ([0, S]) is written first by this kernel
-    e = lr::launch_tile_offsets(out_off, S, P.tile, table, P.err, stream);
+    // every entry of the tables the launch reads is written first by these kernels
+    lr::SkyConst *skyc = v.precision == LR_MIXED ? skytab : nullptr;
+    e = lr::launch_batch_tables(out_off, sky, S, P.tile, table, skyc, P.err, stream);
     if (e) return lr::plan_cuda_fail(plan, e);
+    P.src.skyc = skyc;
     P.src.h_off = h_off;
     P.src.out_off = out_off;
     P.src.t0h = t0_h;

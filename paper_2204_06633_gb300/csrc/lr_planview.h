@@ -14,8 +14,11 @@ struct PlanView {
 int plan_view(const lr_plan *plan, PlanView *v);
 // sets the plan's tile (output samples per CTA) and the window capacities derived from it
 int plan_set_tile(lr_plan *plan, int tile);
-// makes sure the plan's batch tile table holds S+1 entries (may allocate)
+// makes sure the plan's batch tables hold S sources (may allocate): the tile table (S+1
+// entries) and the sources' sky frames
 int plan_reserve_batch(lr_plan *plan, int64_t S);
+// the plan's batch sky-frame table (valid after plan_reserve_batch)
+SkyConst *plan_sky_table(lr_plan *plan);
 // every device allocation of the library (honours lr_debug_fail_allocations)
 cudaError_t dev_malloc(void **p, size_t bytes);
 // records a failing cudaError_t in the plan's context and returns LR_ERR_CUDA

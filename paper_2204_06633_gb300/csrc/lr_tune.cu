@@ -144,10 +144,12 @@ LR_API int lr_plan_autotune(lr_plan *plan, int64_t n_samples, int use_cache, voi
         }
     }
     std::vector<int> cand;
-    const int halo = v.base.HL + v.base.HR;
     if (v.precision == LR_MIXED) {
-        for (int k = 1; k <= 3; ++k)
-            if (k * lr::MIXED_THREADS - halo >= 32) cand.push_back(k * lr::MIXED_THREADS - halo);
+        // the largest tile the shared-memory arrays hold, and smaller ones in steps of 4 outputs
+        const int tmax = lr::mx_max_tile(v.base.HL, v.base.HR, v.base.lproj_b, v.order + 1);
+        cand.push_back(tmax);
+        for (int t : {256, 192, 128})
+            if (t < tmax) cand.push_back(t);
     } else {
         for (int t : {256, 384, 512, 768, 1024}) cand.push_back(t);
     }
@@ -174,6 +176,7 @@ LR_API int lr_plan_autotune(lr_plan *plan, int64_t n_samples, int use_cache, voi
         P.src.nh1 = nh;
         P.src.t0h1 = P.t0 - (double)left * P.dt;
         P.src.sky1 = lr_sky{1.0, 0.3, 0.4};
+        P.src.skyc1 = lr::make_sky(P.src.sky1);
         P.hp = h;
         P.hc = h;
         P.out = out;

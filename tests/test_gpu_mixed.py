@@ -72,10 +72,18 @@ def test_first_generation(ctx, orbits):
     mixed(ctx, src, 20000, 25, orbits["flex"], gen=1)
 
 
-@pytest.mark.parametrize("N,tile", [(1, 0), (7, 0), (255, 256), (257, 256), (1000, 128), (4096, 512)])
+@pytest.mark.parametrize("N,tile", [(1, 0), (7, 0), (255, 256), (257, 256), (1000, 128), (1000, 18), (4096, 340)])
 def test_small_and_ragged(ctx, orbits, N, tile):
+    """Tiles that are not whole TDI items (18) and the largest tile the staged arrays hold (340)."""
     src = synth.draw_sources(1, seed=4, A=1e-21)[0]
     mixed(ctx, src, N, 25, orbits["flex"], tile=tile)
+
+
+def test_tile_beyond_staging_capacity_is_refused(ctx, orbits):
+    """A mixed tile whose link span would not fit the shared-memory arrays is a range error."""
+    with pytest.raises(lr.LRError) as e:
+        lr.Plan(ctx, 25, 4096, DT, orbits["flex"].gpu, t0=T0, precision=lr.MIXED, tile=512)
+    assert e.value.status == 2
 
 
 def test_drawn_sources_per_source_error(ctx, orbits):
