@@ -87,14 +87,14 @@ struct PosPiece {
     float v, a2, a3, pad;
 };
 
-struct MxShared {
+// Everything a tile's compute phases need from its setup: double-buffered, so the setup of a
+// CTA's next tile can run while the current one is processed.
+struct TileSetup {
     TileInfo ti;
-    int64_t s_hint;  // source of the CTA's previous tile
     SkyConst sk;
-    int64_t k_lo;
-    int ny;
-    double u0;
-    unsigned long long maxbits;
+    int64_t k_lo;  // first sample of the link span
+    int ny;        // link span (outputs + TDI halo)
+    double u0;     // strain index of output sample 0
     int wlo, whi;  // extent of the read positions over the span (tile-local samples)
     // read positions: [piece][read], tile-local (strain index - k_lo)
     PosPiece pp[2][9];
@@ -102,14 +102,28 @@ struct MxShared {
     // link delays in samples: [piece][link], output-local index
     PosPiece dp[2][6];
     int jswt, ic;
-    // geometry factors c+_l, cx_l as cubics in tau = (j - jc) 2^-10
+    // geometry factors c+_l, cx_l at the Chebyshev nodes of tau = (j - jc) 2^-10
     double gnode[4][12];
     double tmax, inv_tmax;
+};
+
+struct MxShared {
+    TileSetup ts[2];
+    int64_t tot;     // tiles of the launch
+    int64_t s_hint;  // source of the CTA's latest tile
+    unsigned long long maxbits;
+    double unscale;  // inverse of the current tile's power-of-two scale
+    // geometry factors as cubics in tau (current tile)
     float g0h[12], g0l[12], g1h[12], g2[12], g3[12];
-    // TDI reference per delayed term
+    // TDI reference per delayed term (current tile)
     int tfm[NTERM];
     float tehi[NTERM];
 };
+
+// setup lanes: read-position and link-delay pieces on the first 30 lanes of warp 6, geometry
+// nodes on the first 12 of warp 7 (in fused and projection launches these warps have one
+// projection item and are free for the next tile's setup while the others finish theirs)
+constexpr int SETUP_PIECE0 = 192, SETUP_GEO0 = 224, FIT0 = 96;
 
 // ---------------------------------------------------------------- helpers
 __device__ inline const double *orbit_coef_ptr(const OrbitDev &o, int K, int s)
@@ -314,121 +328,161 @@ __device__ void build_tables(float *smf, int base0, int AS, int SS, int nser, in
 }
 
 // ---------------------------------------------------------------- per-tile setup
-// Threads 0..17: read-position pieces [piece][read] and the span's position extent;
-// threads 32..43: link-delay pieces [piece][link]; threads 64..75: geometry nodes.
+// Tile g's bookkeeping (one thread): source, offsets, sky frame, span.
 template <int KIND>
-__device__ void setup_tile(const FwdParams &P, MxShared &sh)
+__device__ void tile_begin(const FwdParams &P, MxShared &sh, TileSetup &ts, int64_t g)
 {
-    const int tid = threadIdx.x;
-    if (KIND != KIND_TDI && tid < 18) {
-        const OrbitDev &o = P.po;
-        const int ny = sh.ny;
-        const double rstep = P.dt * o.inv_dk;
-        const double ua = (P.t0 + (double)sh.k_lo * P.dt - o.t_first) * o.inv_dk;
-        const double ub = ua + (double)(ny - 1) * rstep;
-        const int K0 = clampK(o, ua), K1 = clampK(o, ub);
-        const int jsw = piece_switch(ua, rstep, K0, K1, ny);
-        const int iv = tid / 9, rd = tid % 9;
-        const int K = iv == 0 ? K0 : K1;
-        const double xa = ua - (double)K;
-        // emission reads (rd >= 3) of link l = rd - 3 shift by the emitter's k.x/c and L_l;
-        // reception reads by the receiver's k.x/c.  position(j) = j + u0 - c(x(j)) samples
-        const int sc = rd < 3 ? rd : (rd == 3 ? 1 : rd == 4 ? 2 : rd == 5 ? 0 : rd == 6 ? 2 : rd == 7 ? 1 : 0);
-        double c[4] = {0.0, 0.0, 0.0, 0.0};
-        const double kc = 1.0 / (C_LIGHT * P.dt);
-        for (int d = 0; d < 3; ++d) {
-            const double *q = orbit_coef_ptr(o, K, 3 * sc + d);
-            for (int i = 0; i < 4; ++i) c[i] = fma(sh.sk.k[d] * kc, q[i], c[i]);
-        }
-        if (rd >= 3) {
-            const double *q = orbit_coef_ptr(o, K, 9 + rd - 3);
-            for (int i = 0; i < 4; ++i) c[i] = fma(q[i], P.inv_dt, c[i]);
-        }
-        const int jc = ny / 2;
-        double d[4];
-        reexpand(c, xa, rstep, jc, d);
-        sh.pp[iv][rd] = make_piece((double)jc + sh.u0 - d[0], 1.0 - d[1], -d[2], -d[3]);
-        // extent of the positions (increasing in j) at the span ends, on the piece holding them
-        if ((0 < jsw) == (iv == 0)) {
-            double p = sh.u0 - horner3(c, xa);
-            p = fmin(fmax(p, -1e8), 1e8);
-            atomicMin(&sh.wlo, (int)floor(p));
-        }
-        if ((ny - 1 < jsw) == (iv == 0)) {
-            double p = (double)(ny - 1) + sh.u0 - horner3(c, fma((double)(ny - 1), rstep, xa));
-            p = fmin(fmax(p, -1e8), 1e8);
-            atomicMax(&sh.whi, (int)floor(p));
-        }
-        if (tid == 0) {
-            sh.jsw = jsw;
-            sh.jc = jc;
-            sh.tmax = ((double)jc + 1.0) * (double)TAU_UNIT;
-            sh.inv_tmax = 1.0 / sh.tmax;
-        }
-    } else if (KIND != KIND_PROJECT && tid >= 32 && tid < 44) {
-        const OrbitDev &o = P.to;
-        const int nb = (int)sh.ti.nb;
-        const double rs = P.dt * o.inv_dk;
-        const double ua = (P.t0 + (double)sh.ti.n0 * P.dt - o.t_first) * o.inv_dk;
-        const double ub = ua + (double)(nb - 1) * rs;
-        const int K0 = clampK(o, ua), K1 = clampK(o, ub);
-        const int iv = (tid - 32) / 6, l = (tid - 32) % 6;
-        const int K = iv == 0 ? K0 : K1;
-        const double *q = orbit_coef_ptr(o, K, 9 + l);
-        double c[4];
-        for (int i = 0; i < 4; ++i) c[i] = q[i] * P.inv_dt;
-        const int ic = nb / 2;
-        double d[4];
-        reexpand(c, ua - (double)K, rs, ic, d);
-        sh.dp[iv][l] = make_piece(d[0], d[1], d[2], d[3]);
-        if (tid == 32) {
-            sh.jswt = piece_switch(ua, rs, K0, K1, nb);
-            sh.ic = ic;
-        }
-    } else if (KIND != KIND_TDI && tid >= 64 && tid < 76) {
-        // geometry factors of arm a at Chebyshev node i (Eq. projected-strain-ssb patterns,
-        // psi rotation, 1/(2(1 -+ k.n)) for the two directions)
-        const OrbitDev &o = P.po;
-        const int i = (tid - 64) / 3, a = (tid - 64) % 3;
-        const double tmax = ((double)(sh.ny / 2) + 1.0) * (double)TAU_UNIT;
-        const double tau = tmax * P.cheb_node[i];
-        const double t = P.t0 + ((double)(sh.k_lo + sh.ny / 2) + tau / (double)TAU_UNIT) * P.dt;
-        double x;
-        const Coef4 *row = spline_row(o, t, &x);
-        const int r = a, s = (a + 1) % 3;
-        double d[3];
-        for (int c = 0; c < 3; ++c) d[c] = cubic(ldg4(row + 3 * r + c), x) - cubic(ldg4(row + 3 * s + c), x);
-        const SkyConst &S = sh.sk;
-        const double inv = rsqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        const double n0 = d[0] * inv, n1 = d[1] * inv, n2 = d[2] * inv;
-        const double un = S.u[0] * n0 + S.u[1] * n1 + S.u[2] * n2;
-        const double vn = S.v[0] * n0 + S.v[1] * n1 + S.v[2] * n2;
-        const double kn = S.k[0] * n0 + S.k[1] * n1 + S.k[2] * n2;
-        const double xip = un * un - vn * vn, xic = 2.0 * un * vn;
-        const double xp = S.c2p * xip + S.s2p * xic, xc = -S.s2p * xip + S.c2p * xic;
-        // 1/(2(1 - kn)) and 1/(2(1 + kn)) from one division
-        const double den = 0.5 / ((1.0 - kn) * (1.0 + kn));
-        const double df = (1.0 + kn) * den, dr = (1.0 - kn) * den;
-        sh.gnode[i][a] = xp * df;
-        sh.gnode[i][6 + a] = xc * df;
-        sh.gnode[i][5 - a] = xp * dr;
-        sh.gnode[i][11 - a] = xc * dr;
+    mx_tile(P, g, KIND == KIND_PROJECT ? 6 : 3, sh.s_hint, ts.ti, ts.sk);
+    if (!ts.ti.ok) atomicOr(P.err, ERR_OFFSETS);
+    const int hl = KIND == KIND_PROJECT ? 0 : P.HL, hr = KIND == KIND_PROJECT ? 0 : P.HR;
+    ts.k_lo = ts.ti.n0 - hl;
+    ts.ny = (int)ts.ti.nb + hl + hr;
+    ts.u0 = (P.t0 - ts.ti.t0h) * P.inv_dt;
+    ts.wlo = INT_MAX;
+    ts.whi = INT_MIN;
+    ts.tmax = ((double)(ts.ny / 2) + 1.0) * (double)TAU_UNIT;
+    ts.inv_tmax = 1.0 / ts.tmax;
+    if (ts.ny > MX_YCAP) {
+        atomicOr(P.err, ERR_WINDOW);
+        ts.ti.ok = 0;
     }
 }
 
-// cubic through the 4 geometry nodes: monomial coefficients in tau from the Chebyshev
-// inverse Vandermonde (threads 96..107)
-__device__ void fit_geometry(const FwdParams &P, MxShared &sh)
+// Setup lane task t in [0, 30): t < 18 the read-position piece [t / 9][read t % 9] with the
+// span's position extent, t >= 18 the link-delay piece [(t - 18) / 6][link (t - 18) % 6].  Both
+// are a cubic c(x) = sum of up to four weighted orbit series on one knot interval, re-expanded
+// around the centre sample: positions j + u0 - c, delays c (samples).  One code path, so the
+// 30 tasks cost one warp's FP64 instruction stream.
+template <int KIND>
+__device__ void setup_piece(const FwdParams &P, TileSetup &ts, int t)
 {
-    const int f = threadIdx.x - 96;
+    const bool pos = t < 18;
+    if (pos ? KIND == KIND_TDI : KIND == KIND_PROJECT) return;
+    const OrbitDev &o = pos ? P.po : P.to;
+    const int n = pos ? ts.ny : (int)ts.ti.nb;
+    const int64_t s0 = pos ? ts.k_lo : ts.ti.n0;
+    const double rstep = P.dt * o.inv_dk;
+    const double ua = (P.t0 + (double)s0 * P.dt - o.t_first) * o.inv_dk;
+    const double ub = ua + (double)(n - 1) * rstep;
+    const int K0 = clampK(o, ua), K1 = clampK(o, ub);
+    const int sw = piece_switch(ua, rstep, K0, K1, n);
+    const int u = pos ? t : t - 18;
+    const int iv = pos ? u / 9 : u / 6;
+    const int K = iv == 0 ? K0 : K1;
+    // emission reads (rd >= 3) of link l = rd - 3 shift by the emitter's k.x/c and L_l;
+    // reception reads by the receiver's k.x/c
+    int ser[4];
+    double w[4];
+    int nt;
+    if (pos) {
+        const int rd = u % 9;
+        const int sc = rd < 3 ? rd : (rd == 3 ? 1 : rd == 4 ? 2 : rd == 5 ? 0 : rd == 6 ? 2 : rd == 7 ? 1 : 0);
+        const double kc = P.inv_dt * (1.0 / C_LIGHT);
+        for (int d = 0; d < 3; ++d) {
+            ser[d] = 3 * sc + d;
+            w[d] = ts.sk.k[d] * kc;
+        }
+        ser[3] = 9 + (rd >= 3 ? rd - 3 : 0);
+        w[3] = P.inv_dt;
+        nt = rd >= 3 ? 4 : 3;
+    } else {
+        ser[0] = 9 + u % 6;
+        w[0] = P.inv_dt;
+        ser[1] = ser[2] = ser[3] = 0;
+        w[1] = w[2] = w[3] = 0.0;
+        nt = 1;
+    }
+    double c[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int v = 0; v < nt; ++v) {
+        const double *q = orbit_coef_ptr(o, K, ser[v]);
+        for (int i = 0; i < 4; ++i) c[i] = fma(w[v], q[i], c[i]);
+    }
+    const int cen = n / 2;
+    double d[4];
+    reexpand(c, ua - (double)K, rstep, cen, d);
+    const double sg = pos ? -1.0 : 1.0;
+    const PosPiece pc = make_piece(fma(sg, d[0], pos ? (double)cen + ts.u0 : 0.0), fma(sg, d[1], pos ? 1.0 : 0.0),
+                                   sg * d[2], sg * d[3]);
+    if (pos) {
+        ts.pp[iv][u % 9] = pc;
+        // extent of the positions (increasing in j) at the span ends, on the piece holding them
+        // (a position outside +-2^18 samples, never a valid one, marks the window as too wide)
+        const long long lim = 1ll << (FX_BITS + 18);
+        if ((0 < sw) == (iv == 0)) {
+            const long long X = piece_at(pc, -cen);
+            atomicMin(&ts.wlo, X > -lim && X < lim ? (int)(X >> FX_BITS) : INT_MIN / 2);
+        }
+        if ((n - 1 < sw) == (iv == 0)) {
+            const long long X = piece_at(pc, n - 1 - cen);
+            atomicMax(&ts.whi, X > -lim && X < lim ? (int)(X >> FX_BITS) : INT_MAX / 2);
+        }
+        if (u == 0) {
+            ts.jsw = sw;
+            ts.jc = cen;
+        }
+    } else {
+        ts.dp[iv][u % 6] = pc;
+        if (u == 0) {
+            ts.jswt = sw;
+            ts.ic = cen;
+        }
+    }
+}
+
+// geometry factors of arm a at Chebyshev node i (Eq. projected-strain-ssb patterns, psi
+// rotation, 1/(2(1 -+ k.n)) for the two directions); task f = 3 i + a in [0, 12)
+__device__ void setup_geometry(const FwdParams &P, TileSetup &ts, int f)
+{
+    const OrbitDev &o = P.po;
+    const int i = f / 3, a = f % 3;
+    const double tau = ts.tmax * P.cheb_node[i];
+    const double t = P.t0 + ((double)(ts.k_lo + ts.ny / 2) + tau / (double)TAU_UNIT) * P.dt;
+    double x;
+    const Coef4 *row = spline_row(o, t, &x);
+    const int r = a, s = (a + 1) % 3;
+    double d[3];
+    for (int c = 0; c < 3; ++c) d[c] = cubic(ldg4(row + 3 * r + c), x) - cubic(ldg4(row + 3 * s + c), x);
+    const SkyConst &S = ts.sk;
+    const double inv = rsqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const double n0 = d[0] * inv, n1 = d[1] * inv, n2 = d[2] * inv;
+    const double un = S.u[0] * n0 + S.u[1] * n1 + S.u[2] * n2;
+    const double vn = S.v[0] * n0 + S.v[1] * n1 + S.v[2] * n2;
+    const double kn = S.k[0] * n0 + S.k[1] * n1 + S.k[2] * n2;
+    const double xip = un * un - vn * vn, xic = 2.0 * un * vn;
+    const double xp = S.c2p * xip + S.s2p * xic, xc = -S.s2p * xip + S.c2p * xic;
+    // 1/(2(1 - kn)) and 1/(2(1 + kn)) from one division
+    const double den = 0.5 / ((1.0 - kn) * (1.0 + kn));
+    const double df = (1.0 + kn) * den, dr = (1.0 - kn) * den;
+    ts.gnode[i][a] = xp * df;
+    ts.gnode[i][6 + a] = xc * df;
+    ts.gnode[i][5 - a] = xp * dr;
+    ts.gnode[i][11 - a] = xc * dr;
+}
+
+// the setup lanes of a tile (see SETUP_PIECE0)
+template <int KIND>
+__device__ __forceinline__ void setup_lanes(const FwdParams &P, TileSetup &ts)
+{
+    const int tid = threadIdx.x;
+    if (tid >= SETUP_PIECE0 && tid < SETUP_PIECE0 + 30)
+        setup_piece<KIND>(P, ts, tid - SETUP_PIECE0);
+    else if (KIND != KIND_TDI && tid >= SETUP_GEO0 && tid < SETUP_GEO0 + 12)
+        setup_geometry(P, ts, tid - SETUP_GEO0);
+}
+
+// cubic through the 4 geometry nodes: monomial coefficients in tau from the Chebyshev
+// inverse Vandermonde (threads FIT0 .. FIT0 + 11)
+__device__ void fit_geometry(const FwdParams &P, const TileSetup &ts, MxShared &sh)
+{
+    const int f = threadIdx.x - FIT0;
     if (f < 0 || f >= 12) return;
     double b[4];
     double sc = 1.0;
     for (int k = 0; k < 4; ++k) {
         double acc = 0.0;
-        for (int i = 0; i < 4; ++i) acc = fma(P.cheb[k][i], sh.gnode[i][f], acc);
+        for (int i = 0; i < 4; ++i) acc = fma(P.cheb[k][i], ts.gnode[i][f], acc);
         b[k] = acc * sc;
-        sc *= sh.inv_tmax;
+        sc *= ts.inv_tmax;
     }
     const ff c0 = ff_from_double(b[0]);
     sh.g0h[f] = c0.hi;
@@ -440,18 +494,19 @@ __device__ void fit_geometry(const FwdParams &P, MxShared &sh)
 
 // Reference of each delayed TDI term at the tile centre ic (its chained delay is the sum of the
 // pieces' centre values, exactly what the delay table holds at ic) and the correction weights
-// there with their derivative, interleaved as (U_a, dU_a/deps) pairs (threads 128..169).
+// there with their derivative, interleaved as (U_a, dU_a/deps) pairs (the last 42 threads: in
+// fused launches they run it after their one projection item, beside the others' second).
 template <int T>
-__device__ void tdi_refs(const FwdParams &P, MxShared &sh, float *tw)
+__device__ void tdi_refs(const FwdParams &P, const TileSetup &ts, MxShared &sh, float *tw)
 {
-    const int id = threadIdx.x - 128;
+    const int id = threadIdx.x - (MIXED_THREADS - NTERM);
     if (id < 0 || id >= NTERM) return;
     const int ch = id / 14, c = (id / 7) % 2, q = id % 7 + 1;
     if (q > P.q_terms) return;
-    const int iv = sh.ic < sh.jswt ? 0 : 1;
+    const int iv = ts.ic < ts.jswt ? 0 : 1;
     long long D = 0;
-    for (int k = 1; k <= q; ++k) D += sh.dp[iv][chain_pair(ch, c, k)].Xc;
-    const int nlr = sh.ic + P.HL;
+    for (int k = 1; k <= q; ++k) D += ts.dp[iv][c_tdimx.pair[ch][c][k]].Xc;
+    const int nlr = ts.ic + P.HL;
     const Split s = split_fx(((long long)nlr << FX_BITS) - D);
     sh.tfm[id] = s.m - nlr;
     sh.tehi[id] = s.ehi;
@@ -512,7 +567,7 @@ __device__ __forceinline__ void store_read(float *smf, int rd, int pol, int j, f
 // inside the item, or that straddle a knot of the orbit spline.  Out-of-window stencils read 0
 // and record ERR_WINDOW.
 template <int T>
-__device__ __noinline__ void proj_item_exact(float *smf, const MxShared &sh, int rd, int j0, int kmax, int wlen,
+__device__ __noinline__ void proj_item_exact(float *smf, const TileSetup &sh, int rd, int j0, int kmax, int wlen,
                                              long long woff_fx, int *err)
 {
     constexpr int h = (T - 2) / 2;
@@ -541,7 +596,7 @@ __device__ __noinline__ void proj_item_exact(float *smf, const MxShared &sh, int
 
 // Projection item: read rd at the samples j0 .. j0+7 of the span.
 template <int T>
-__device__ __forceinline__ void proj_item(float *smf, const MxShared &sh, int rd, int b, int ny, int wlen,
+__device__ __forceinline__ void proj_item(float *smf, const TileSetup &sh, int rd, int b, int ny, int wlen,
                                           long long woff_fx, int *err)
 {
     constexpr int h = (T - 2) / 2;
@@ -677,7 +732,7 @@ __device__ __noinline__ void tdi_read_exact(const float *smf, int lk, int m, flo
 // dk, so output k reads at index m0 + k with fraction eh + (el - dk 2^-44) while that stays
 // in [0, 1).
 template <int T, int SG>
-__device__ __forceinline__ void tdi_chain(const FwdParams &P, const MxShared &sh, const float *smf,
+__device__ __forceinline__ void tdi_chain(const FwdParams &P, const MxShared &sh, int ny, const float *smf,
                                           const long long *Lblk, const float *dLf, int ch, int b, int kmax,
                                           float *hi, float *lo, float *sm)
 {
@@ -686,7 +741,6 @@ __device__ __forceinline__ void tdi_chain(const FwdParams &P, const MxShared &sh
     constexpr int NU = T >= 4 ? T - 3 : 1;
     constexpr int NE = NU + TB - 1;
     constexpr int NUP = mx_nup(T);
-    const int ny = sh.ny;
     const int i0 = TB * b;
     const int nl0 = i0 + P.HL;
     {
@@ -791,74 +845,90 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
     extern __shared__ __align__(16) float smf[];
     __shared__ MxShared sh;
     constexpr int h = (T - 2) / 2;
-    const int64_t tot = P.total_tiles >= 0 ? P.total_tiles : P.src.tile_off[P.src.S];
-    if (threadIdx.x == 0) sh.s_hint = 0;
-    for (int64_t g = blockIdx.x; g < tot; g += gridDim.x) {
-        if (threadIdx.x == 0) {
-            mx_tile(P, g, KIND == KIND_PROJECT ? 6 : 3, sh.s_hint, sh.ti, sh.sk);
-            if (!sh.ti.ok) atomicOr(P.err, ERR_OFFSETS);
-            const int hl = KIND == KIND_PROJECT ? 0 : P.HL, hr = KIND == KIND_PROJECT ? 0 : P.HR;
-            sh.k_lo = sh.ti.n0 - hl;
-            sh.ny = (int)sh.ti.nb + hl + hr;
-            sh.u0 = (P.t0 - sh.ti.t0h) / P.dt;
-            sh.maxbits = 0ull;
-            sh.wlo = INT_MAX;
-            sh.whi = INT_MIN;
-            if (sh.ny > MX_YCAP) {
-                atomicOr(P.err, ERR_WINDOW);
-                sh.ti.ok = 0;
-            }
-        }
+    // fused and projection launches set up the CTA's next tile on the warps a projection phase
+    // leaves idle; TDI-only launches set up each tile in place
+    constexpr bool PREFETCH = KIND != KIND_TDI;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        sh.tot = P.total_tiles >= 0 ? P.total_tiles : P.src.tile_off[P.src.S];
+        sh.s_hint = 0;
+        sh.maxbits = 0ull;
+    }
+    __syncthreads();
+    int cur = 0;
+    if (PREFETCH && blockIdx.x < sh.tot) {
+        if (tid == 0) tile_begin<KIND>(P, sh, sh.ts[0], blockIdx.x);
         __syncthreads();
-        if (!sh.ti.ok || sh.ti.nb <= 0) {
+        if (sh.ts[0].ti.ok && sh.ts[0].ti.nb > 0) setup_lanes<KIND>(P, sh.ts[0]);
+        __syncthreads();
+    }
+    for (int64_t g = blockIdx.x; g < sh.tot; g += gridDim.x, cur ^= PREFETCH ? 1 : 0) {
+        TileSetup &ts = sh.ts[cur];
+        TileSetup &tn = sh.ts[cur ^ 1];
+        const int64_t gn = g + gridDim.x;
+        const bool next = PREFETCH && gn < sh.tot;
+        if (!PREFETCH) {
+            if (tid == 0) tile_begin<KIND>(P, sh, ts, g);
+            __syncthreads();
+            if (ts.ti.ok && ts.ti.nb > 0) setup_lanes<KIND>(P, ts);
+            __syncthreads();
+        }
+        if (!ts.ti.ok || ts.ti.nb <= 0) {
+            if (next) {
+                if (tid == 0) tile_begin<KIND>(P, sh, tn, gn);
+                __syncthreads();
+                if (tn.ti.ok && tn.ti.nb > 0) setup_lanes<KIND>(P, tn);
+            }
             __syncthreads();
             continue;
         }
-        const int ny = sh.ny, nb = (int)sh.ti.nb;
-        // ---- setup
-        setup_tile<KIND>(P, sh);
-        __syncthreads();
-        // ---- stage raw inputs and their maximum; geometry fit; TDI references
+        const int ny = ts.ny, nb = (int)ts.ti.nb;
+        // ---- stage raw inputs and their maximum; geometry fit; TDI references (TDI-only);
+        //      bookkeeping of the next tile
         int wlen = 0;
         long long woff_fx = 0;
         if (KIND != KIND_TDI) {
-            const long long span = (long long)sh.whi - (long long)sh.wlo + T + 4;
-            wlen = span > 0 && span <= MX_WCAP ? (int)span : MX_WCAP;
-            if (!(span > 0 && span <= MX_WCAP) && threadIdx.x == 0) atomicOr(P.err, ERR_WINDOW);
-            const int woff = sh.wlo - h - 2;
+            const long long span = (long long)ts.whi - (long long)ts.wlo + T + 4;
+            const bool wok = span > 0 && span <= MX_WCAP;
+            wlen = wok ? (int)span : MX_WCAP;
+            if (!wok && tid == 0) atomicOr(P.err, ERR_WINDOW);
+            const int woff = wok ? ts.wlo - h - 2 : 0;
             woff_fx = (long long)woff << FX_BITS;
             double *tmp = reinterpret_cast<double *>(smf + OFF_Y);
             unsigned long long mx = 0ull;
-            for (int j = threadIdx.x; j < wlen; j += blockDim.x) {
-                const int64_t i = sh.k_lo + woff + j;
-                const bool in = i >= 0 && i < sh.ti.nh;
-                const double a = in ? __ldg(sh.ti.hp + i) : 0.0, b = in ? __ldg(sh.ti.hc + i) : 0.0;
+            for (int j = tid; j < wlen; j += blockDim.x) {
+                const int64_t i = ts.k_lo + woff + j;
+                const bool in = i >= 0 && i < ts.ti.nh;
+                const double a = in ? __ldg(ts.ti.hp + i) : 0.0, b = in ? __ldg(ts.ti.hc + i) : 0.0;
                 tmp[j] = a;
                 tmp[MX_WCAP + j] = b;
                 mx = max(mx, max(abs_bits(a), abs_bits(b)));
             }
             block_absmax(&sh.maxbits, mx);
-            fit_geometry(P, sh);
+            fit_geometry(P, ts, sh);
         } else {
             double *tmp = reinterpret_cast<double *>(smf + OFF_W);
             unsigned long long mx = 0ull;
             for (int l = 0; l < 6; ++l)
-                for (int j = threadIdx.x; j < ny; j += blockDim.x) {
-                    const int64_t k = sh.k_lo + j;
-                    const double v = (k >= 0 && k < sh.ti.N) ? __ldg(sh.ti.yin + l * sh.ti.N + k) : 0.0;
+                for (int j = tid; j < ny; j += blockDim.x) {
+                    const int64_t k = ts.k_lo + j;
+                    const double v = (k >= 0 && k < ts.ti.N) ? __ldg(ts.ti.yin + l * ts.ti.N + k) : 0.0;
                     tmp[l * MX_YCAP + j] = v;
                     mx = max(mx, abs_bits(v));
                 }
             block_absmax(&sh.maxbits, mx);
+            tdi_refs<T>(P, ts, sh, smf + OFF_TW);
         }
-        if (KIND != KIND_PROJECT) tdi_refs<T>(P, sh, smf + OFF_TW);
+        if (next && tid == MIXED_THREADS - 1) tile_begin<KIND>(P, sh, tn, gn);
         __syncthreads();
         // ---- scaled float-float values
-        double scale, unscale;
-        tile_scale(sh.maxbits, scale, unscale);
+        {
+            double scale, unscale;
+            tile_scale(sh.maxbits, scale, unscale);
+            if (tid == 0) sh.unscale = unscale;
         if (KIND != KIND_TDI) {
             const double *tmp = reinterpret_cast<const double *>(smf + OFF_Y);
-            for (int j = threadIdx.x; j < wlen; j += blockDim.x) {
+            for (int j = tid; j < wlen; j += blockDim.x) {
                 const ff a = ff_from_double(tmp[j] * scale), b = ff_from_double(tmp[MX_WCAP + j] * scale);
                 const int p = phw(j);
                 smf[warr(0, A_SHI) + p] = a.hi;
@@ -869,26 +939,31 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
         } else {
             const double *tmp = reinterpret_cast<const double *>(smf + OFF_W);
             for (int l = 0; l < 6; ++l)
-                for (int j = threadIdx.x; j < ny; j += blockDim.x) {
+                for (int j = tid; j < ny; j += blockDim.x) {
                     const ff v = ff_from_double(tmp[l * MX_YCAP + j] * scale);
                     smf[ybase(l) + A_SHI * MX_AY + phy(j)] = v.hi;
                     smf[ybase(l) + A_SLO * MX_AY + phy(j)] = v.lo;
                 }
         }
+        }
         __syncthreads();
+        if (tid == 0) sh.maxbits = 0ull;  // every thread has read it
         long long *Lblk = reinterpret_cast<long long *>(smf + OFF_W);
         float *dLf = smf + OFF_W + 2 * 6 * LB;
         if (KIND != KIND_TDI) {
             // ---- strain difference tables
             build_tables<true, RLW>(smf, warr(0, A_SHI), MX_AW, 7 * MX_AW, 2, wlen);
             __syncthreads();
-            // ---- projection reads
+            // ---- projection reads; then, on the warps with one item: the TDI references and
+            //      the next tile's setup
             const int nblk = (ny + PB - 1) / PB;
-            for (int it = threadIdx.x; it < 9 * nblk; it += blockDim.x)
-                proj_item<T>(smf, sh, it / nblk, it % nblk, ny, wlen, woff_fx, P.err);
+            for (int it = tid; it < 9 * nblk; it += blockDim.x)
+                proj_item<T>(smf, ts, it / nblk, it % nblk, ny, wlen, woff_fx, P.err);
+            if (KIND == KIND_FUSED) tdi_refs<T>(P, ts, sh, smf + OFF_TW);
+            if (next && tn.ti.ok && tn.ti.nb > 0) setup_lanes<KIND>(P, tn);
             __syncthreads();
-            // ---- link series (in place over the staged reads) and the tile's link delays
-            for (int j = threadIdx.x; j < ny; j += blockDim.x) {
+            // ---- link series (in place over the staged reads)
+            for (int j = tid; j < ny; j += blockDim.x) {
                 const int ai = phy(j);
                 ff rp[3], rc[3];
 #pragma unroll
@@ -896,7 +971,7 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
                     rp[r] = {smf[OFF_Y + (4 * r + 0) * MX_AY + ai], smf[OFF_Y + (4 * r + 1) * MX_AY + ai]};
                     rc[r] = {smf[OFF_Y + (4 * r + 2) * MX_AY + ai], smf[OFF_Y + (4 * r + 3) * MX_AY + ai]};
                 }
-                const float tau = (float)(j - sh.jc) * TAU_UNIT;
+                const float tau = (float)(j - ts.jc) * TAU_UNIT;
                 ff y[6];
 #pragma unroll
                 for (int l = 0; l < 6; ++l) {
@@ -907,14 +982,14 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
                     y[l] = ff_add(ff_mul(geom_at(sh, l, tau), ff_sub(ep, rp[r])),
                                   ff_mul(geom_at(sh, 6 + l, tau), ff_sub(ec, rc[r])));
                 }
-                const int64_t k = sh.k_lo + j;
+                const int64_t k = ts.k_lo + j;
                 if (KIND == KIND_PROJECT) {
-                    double *o = sh.ti.out;
-                    const int64_t N = sh.ti.N;
+                    double *o = ts.ti.out;
+                    const int64_t N = ts.ti.N;
 #pragma unroll
-                    for (int l = 0; l < 6; ++l) o[l * N + k] = ff_to_double(y[l]) * unscale;
+                    for (int l = 0; l < 6; ++l) o[l * N + k] = ff_to_double(y[l]) * sh.unscale;
                 } else {
-                    const bool in = k >= 0 && k < sh.ti.N;
+                    const bool in = k >= 0 && k < ts.ti.N;
 #pragma unroll
                     for (int l = 0; l < 6; ++l) {
                         smf[ybase(l) + A_SHI * MX_AY + ai] = in ? y[l].hi : 0.0f;
@@ -927,10 +1002,10 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
             // link delays of the outputs: at each item's first output (fixed point) and the
             // increments to the item's other outputs (rows padded to whole items)
             const int nb4 = (nb + TB - 1) & ~(TB - 1);
-            for (int idx = threadIdx.x; idx < 6 * nb4; idx += blockDim.x) {
+            for (int idx = tid; idx < 6 * nb4; idx += blockDim.x) {
                 const int l = idx / nb4, i = idx - l * nb4, i0 = i & ~(TB - 1);
-                const long long Li = piece_at(sh.dp[i < sh.jswt ? 0 : 1][l], i - sh.ic);
-                const long long L0 = piece_at(sh.dp[i0 < sh.jswt ? 0 : 1][l], i0 - sh.ic);
+                const long long Li = piece_at(ts.dp[i < ts.jswt ? 0 : 1][l], i - ts.ic);
+                const long long L0 = piece_at(ts.dp[i0 < ts.jswt ? 0 : 1][l], i0 - ts.ic);
                 dLf[l * LT + i] = (float)(Li - L0);
                 if (i == i0) Lblk[l * LB + i / TB] = Li;
             }
@@ -940,18 +1015,18 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
             __syncthreads();
             // ---- X, Y, Z
             const int nbb = (nb + TB - 1) / TB;
-            for (int it = threadIdx.x; it < 3 * nbb; it += blockDim.x) {
+            for (int it = tid; it < 3 * nbb; it += blockDim.x) {
                 const int ch = it / nbb, b = it - ch * nbb, i0 = TB * b;
                 const int kmax = min(TB, nb - i0);
                 float hi[TB], lo[TB], sm[TB];
 #pragma unroll
                 for (int k = 0; k < TB; ++k) hi[k] = lo[k] = sm[k] = 0.0f;
-                tdi_chain<T, 1>(P, sh, smf, Lblk, dLf, ch, b, kmax, hi, lo, sm);
-                tdi_chain<T, -1>(P, sh, smf, Lblk, dLf, ch, b, kmax, hi, lo, sm);
-                double *o = sh.ti.out + ch * sh.ti.N + sh.ti.n0 + i0;
+                tdi_chain<T, 1>(P, sh, ny, smf, Lblk, dLf, ch, b, kmax, hi, lo, sm);
+                tdi_chain<T, -1>(P, sh, ny, smf, Lblk, dLf, ch, b, kmax, hi, lo, sm);
+                double *o = ts.ti.out + ch * ts.ti.N + ts.ti.n0 + i0;
 #pragma unroll
                 for (int k = 0; k < TB; ++k)
-                    if (k < kmax) o[k] = ((double)hi[k] + (double)(lo[k] + sm[k])) * unscale;
+                    if (k < kmax) o[k] = ((double)hi[k] + (double)(lo[k] + sm[k])) * sh.unscale;
             }
         }
         __syncthreads();

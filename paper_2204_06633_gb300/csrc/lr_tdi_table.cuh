@@ -39,22 +39,4 @@ __host__ __device__ constexpr TdiTab make_tdi_tab()
     return t;
 }
 
-// The same tables as pure functions of (channel, chain, term), for loops the compiler unrolls:
-// link read by term q and link whose delay term q adds.
-__host__ __device__ constexpr int chain_seq(int c, int q)
-{
-    return c == 0 ? (q == 0 ? 1 : q == 1 ? 3 : q == 2 ? 1 : q == 3 ? 2 : q == 4 ? 1 : q == 5 ? 2 : q == 6 ? 1 : q == 7 ? 3 : 1)
-                  : (q == 0 ? 1 : q == 1 ? 2 : q == 2 ? 1 : q == 3 ? 3 : q == 4 ? 1 : q == 5 ? 3 : q == 6 ? 1 : q == 7 ? 2 : 1);
-}
-
-__host__ __device__ constexpr int chain_link(int ch, int c, int q)
-{
-    return link_of(cyc(chain_seq(c, q), ch), cyc(chain_seq(c, q + 1), ch));
-}
-
-__host__ __device__ constexpr int chain_pair(int ch, int c, int q)
-{
-    return link_of(cyc(chain_seq(c, q - 1), ch), cyc(chain_seq(c, q), ch));
-}
-
 }  // namespace lr
