@@ -649,28 +649,50 @@ __device__ __forceinline__ void proj_item(float *smf, const TileSetup &sh, int r
 #pragma unroll
     for (int r = 0; r < 8; ++r) o[r] = phw(x + r);
     const float eref = kmax == PB ? eh[PB / 2] : eh[0];
-    float U0[NU], U1[NU];
-    if constexpr (T >= 4) comp_weights_d<T>(eref, U0, U1);
+    // correction weights and their derivative as packed (U_a, dU_a/deps) pairs
+    unsigned long long W[NU];
+    if constexpr (T >= 4) {
+        float U0[NU], U1[NU];
+        comp_weights_d<T>(eref, U0, U1);
+#pragma unroll
+        for (int a = 0; a < NU; ++a) W[a] = f2pack(U0[a], U1[a]);
+    }
 #pragma unroll
     for (int pol = 0; pol < 2; ++pol) {
-        float E[NE];
+        float C[PB];
         if constexpr (T >= 4) {
+            // FIR with packed pairs over a sliding window of (e, e): at tap a the samples
+            // k = 0..7 read e[k + a]; only the 8 entries e[a .. a+7] are live
+            unsigned long long acc[PB], win[PB];
 #pragma unroll
-            for (int a = 0; a < NE; ++a) E[a] = smf[warr(pol, A_E) + o[a & 7] + (a >> 3)];
+            for (int k = 0; k < PB; ++k) {
+                acc[k] = 0ull;
+                const float v = smf[warr(pol, A_E) + o[k & 7] + (k >> 3)];
+                win[k] = f2pack(v, v);
+            }
+#pragma unroll
+            for (int a = 0; a < NU; ++a) {
+#pragma unroll
+                for (int k = 0; k < PB; ++k) acc[k] = ffma2(W[a], win[(a + k) % PB], acc[k]);
+                if (a + PB < NE) {
+                    const int e = a + PB;  // replaces e[a], no longer read
+                    const float v = smf[warr(pol, A_E) + o[e & 7] + (e >> 3)];
+                    win[a % PB] = f2pack(v, v);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < PB; ++k) {
+                float c0, c1;
+                f2unpack(acc[k], c0, c1);
+                C[k] = fmaf((eh[k] - eref) + el[k], c1, c0);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < PB; ++k) C[k] = 0.0f;
         }
 #pragma unroll
         for (int k = 0; k < PB; ++k) {
-            float C = 0.0f;
-            if constexpr (T >= 4) {
-                float c0 = 0.0f, c1 = 0.0f;
-#pragma unroll
-                for (int a = 0; a < NU; ++a) {
-                    c0 = fmaf(U0[a], E[k + a], c0);
-                    c1 = fmaf(U1[a], E[k + a], c1);
-                }
-                C = fmaf((eh[k] - eref) + el[k], c1, c0);
-            }
-            const ff v = strain_anchor<T>(smf, pol, o[(h + k) & 7] + ((h + k) >> 3), eh[k], el[k], C);
+            const ff v = strain_anchor<T>(smf, pol, o[(h + k) & 7] + ((h + k) >> 3), eh[k], el[k], C[k]);
             if (k < kmax) store_read(smf, rd, pol, j0 + k, v);
         }
     }
@@ -790,11 +812,13 @@ __device__ __forceinline__ void tdi_chain(const FwdParams &P, const MxShared &sh
             for (int k = 0; k < TB; ++k) C[k] = 0.0f;
             if constexpr (T >= 4) {
                 const float dref = eh - sh.tehi[id];
-                unsigned long long ee[NE];  // (e, e) pairs of the window
+                // (e, e) pairs of the window in a ring of RW: taps a, a+1 read e[a .. a+TB]
+                constexpr int RW = TB + 2;
+                unsigned long long win[RW];
 #pragma unroll
-                for (int a = 0; a < NE; ++a) {
-                    const float v = smf[yb + A_E * MX_AY + o[a & 7] + (a >> 3)];
-                    ee[a] = f2pack(v, v);
+                for (int a = 0; a < RW; ++a) {
+                    const float v = a < NE ? smf[yb + A_E * MX_AY + o[a & 7] + (a >> 3)] : 0.0f;
+                    win[a] = f2pack(v, v);
                 }
                 unsigned long long acc[TB];  // (sum U e, sum dU e)
 #pragma unroll
@@ -802,12 +826,19 @@ __device__ __forceinline__ void tdi_chain(const FwdParams &P, const MxShared &sh
                 const ulonglong2 *w = reinterpret_cast<const ulonglong2 *>(smf + OFF_TW) + id * (NUP / 2);
 #pragma unroll
                 for (int a2 = 0; a2 < NUP / 2; ++a2) {
-                    const ulonglong2 u = w[a2];  // (U, dU) at taps 2 a2 and 2 a2 + 1
+                    const int a = 2 * a2;
+                    const ulonglong2 u = w[a2];  // (U, dU) at taps a and a + 1
 #pragma unroll
                     for (int k = 0; k < TB; ++k) {
-                        acc[k] = ffma2(u.x, ee[k + 2 * a2], acc[k]);
-                        if (2 * a2 + 1 < NU) acc[k] = ffma2(u.y, ee[k + 2 * a2 + 1], acc[k]);
+                        acc[k] = ffma2(u.x, win[(a + k) % RW], acc[k]);
+                        if (a + 1 < NU) acc[k] = ffma2(u.y, win[(a + 1 + k) % RW], acc[k]);
                     }
+#pragma unroll
+                    for (int e = a + RW; e < a + RW + 2; ++e)  // e[a], e[a+1] are no longer read
+                        if (e < NE) {
+                            const float v = smf[yb + A_E * MX_AY + o[e & 7] + (e >> 3)];
+                            win[e % RW] = f2pack(v, v);
+                        }
                 }
 #pragma unroll
                 for (int k = 0; k < TB; ++k) {
