@@ -102,19 +102,20 @@ struct TileSetup {
     // link delays in samples: [piece][link], output-local index
     PosPiece dp[2][6];
     int jswt, ic;
-    // geometry factors c+_l, cx_l at the Chebyshev nodes of tau = (j - jc) 2^-10
+    // geometry factors c+_l, cx_l at the Chebyshev nodes of tau = (j - jc) 2^-10, and as cubics
+    // in tau (constant in float-float)
     double gnode[4][12];
     double tmax, inv_tmax;
+    float g0h[12], g0l[12], g1[12], g2[12], g3[12];
+    // maximum of the tile's raw inputs (bit pattern)
+    unsigned long long maxbits;
 };
 
 struct MxShared {
     TileSetup ts[2];
     int64_t tot;     // tiles of the launch
     int64_t s_hint;  // source of the CTA's latest tile
-    unsigned long long maxbits;
-    double unscale;  // inverse of the current tile's power-of-two scale
-    // geometry factors as cubics in tau (current tile)
-    float g0h[12], g0l[12], g1h[12], g2[12], g3[12];
+    int unscale_e;   // exponent of the inverse of the current tile's power-of-two scale
     // TDI reference per delayed term (current tile)
     int tfm[NTERM];
     float tehi[NTERM];
@@ -123,7 +124,7 @@ struct MxShared {
 // setup lanes: read-position and link-delay pieces on the first 30 lanes of warp 6, geometry
 // nodes on the first 12 of warp 7 (in fused and projection launches these warps have one
 // projection item and are free for the next tile's setup while the others finish theirs)
-constexpr int SETUP_PIECE0 = 192, SETUP_GEO0 = 224, FIT0 = 96;
+constexpr int SETUP_PIECE0 = 192, SETUP_GEO0 = 224;
 
 // ---------------------------------------------------------------- helpers
 __device__ inline const double *orbit_coef_ptr(const OrbitDev &o, int K, int s)
@@ -237,12 +238,6 @@ __device__ inline void mx_tile(const FwdParams &P, int64_t g, int ochan, int64_t
     if (ti.nb < 0) ti.nb = 0;
 }
 
-// value of a fitted geometry factor at tau: the constant in float-float, the variation over the
-// tile (a relative 1e-4 at most) in FP32
-__device__ __forceinline__ ff geom_at(const MxShared &sh, int f, float tau)
-{
-    return ff_add_f({sh.g0h[f], sh.g0l[f]}, tau * fmaf(tau, fmaf(tau, sh.g3[f], sh.g2[f]), sh.g1h[f]));
-}
 
 // block max of the bit patterns b of |v| (for non-negative doubles the order of the patterns is
 // the order of the values; a NaN orders above every finite value)
@@ -261,43 +256,81 @@ __device__ inline void block_absmax(unsigned long long *dst, unsigned long long 
     if ((threadIdx.x & 31) == 0) atomicMax(dst, b);
 }
 
-// power-of-two scale putting the tile's largest value in [1/2, 1), built from the exponent
-// bits of the maximum (integer work only); 1 for a zero, subnormal or non-finite maximum
-__device__ __forceinline__ void tile_scale(unsigned long long maxbits, double &scale, double &unscale)
+// exponent se of the power-of-two scale 2^se putting the tile's largest value in [1/2, 1),
+// from the exponent bits of the maximum; 0 for a zero, subnormal or non-finite maximum
+__device__ __forceinline__ int tile_scale_exp(unsigned long long maxbits)
 {
-    const long long eb = (long long)((maxbits >> 52) & 0x7ffull);  // max = f 2^(eb - 1022), f in [1/2, 1)
-    const bool ok = eb >= 1 && eb <= 2044;
-    scale = ok ? __longlong_as_double((2045 - eb) << 52) : 1.0;
-    unscale = ok ? __longlong_as_double((eb + 1) << 52) : 1.0;
+    const int eb = (int)((maxbits >> 52) & 0x7ffull);  // max = f 2^(eb - 1022), f in [1/2, 1)
+    return eb >= 1 && eb <= 2044 ? 1022 - eb : 0;
 }
+
+// x 2^se as float-float by integer work on the bit pattern: hi holds x's 24 leading significand
+// bits (truncated) with the exponent moved by se, lo the remaining 29 bits rounded to FP32.
+// Values whose scaled hi falls below the FP32 normal range read as zero (below 2^-126 of the
+// scaled tile maximum); an infinity or NaN passes through in hi.
+__device__ __forceinline__ ff ff_from_double_scaled(double x, int se)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned sg = (unsigned)(b >> 32) & 0x80000000u;
+    const int ex = (int)((b >> 52) & 0x7ffull);
+    const unsigned long long m = b & 0xfffffffffffffull;
+    if (ex == 0x7ff) return {__uint_as_float(sg | 0x7f800000u | (m ? 0x400000u : 0u)), 0.0f};
+    const int eh = ex - 896 + se;  // FP32 biased exponent of hi (1023 - 127 = 896)
+    if (ex == 0 || eh <= 0) return {__uint_as_float(sg), 0.0f};
+    if (eh >= 255) return {__uint_as_float(sg | 0x7f800000u), 0.0f};
+    const float hi = __uint_as_float(sg | ((unsigned)eh << 23) | (unsigned)(m >> 29));
+    // remainder r 2^(eh - 127 - 52); zero once that power leaves the normal range (2^-75 of
+    // the scaled maximum at most)
+    const unsigned r = (unsigned)(m & 0x1fffffffu);
+    const int el = eh - 52;
+    const float lo = el > 0 ? __uint2float_rn(r) * __uint_as_float((unsigned)el << 23) : 0.0f;
+    return {hi, sg ? -lo : lo};
+}
+
+// f 2^se as a double by integer work (zero and subnormal f read as signed zero: they are below
+// 2^-126 of the scaled tile maximum)
+__device__ __forceinline__ double f2d_scaled(float f, int se)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xffu;
+    if (e == 0xffu) return (double)f;
+    const unsigned long long sgn = (unsigned long long)(b & 0x80000000u) << 32;
+    if (e == 0u) return __longlong_as_double((long long)sgn);
+    return __longlong_as_double(
+        (long long)(sgn | ((unsigned long long)((int)e + 896 + se) << 52) | ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+
+// float-float (hi, lo) 2^se as a double: exact conversions of both parts, one FP64 add
+__device__ __forceinline__ double ff2d_scaled(float hi, float lo, int se) { return f2d_scaled(hi, se) + f2d_scaled(lo, se); }
+
 
 // Difference tables of a staged float-float series (arrays at base + k * AS, 8-phase index
 // with row length RL): d = s_{j+1} - s_j and a = (d_j - d_{j-1})/2 in float-float (ALO: the low
 // part of a kept in its own array, else folded into a), e = d_{j+2} - 2 d_{j+1} + d_j in FP32.
-// Each thread forms 4 consecutive entries of one of the nser series (series stride SS) from one
+// Each thread forms Q consecutive entries of one of the nser series (series stride SS) from one
 // set of differences.  Entries whose stencils leave [0, len) are 0; no read ever uses them.
-template <bool ALO, int RL>
+template <bool ALO, int RL, int Q>
 __device__ void build_tables(float *smf, int base0, int AS, int SS, int nser, int len)
 {
     auto at = [](int i) { return (i & 7) * RL + (i >> 3); };
-    const int nq = (len + 3) / 4;
+    const int nq = (len + Q - 1) / Q;
     for (int it = threadIdx.x; it < nser * nq; it += blockDim.x) {
         const int ser = it / nq, t = it - ser * nq;
         const int base = base0 + ser * SS;
-        const int j0 = 4 * t;
-        ff s[8];  // s_{j0-1} .. s_{j0+6}
+        const int j0 = Q * t;
+        ff s[Q + 4];  // s_{j0-1} .. s_{j0+Q+2}
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < Q + 4; ++u) {
             const int i = j0 - 1 + u;
             s[u] = (i >= 0 && i < len) ? ff{smf[base + at(i)], smf[base + AS + at(i)]} : ff{0.0f, 0.0f};
         }
-        ff d[7], dd[6];  // d_{j0-1+u}, dd_{j0-1+u} = d_{j0+u} - d_{j0-1+u}
+        ff d[Q + 3], dd[Q + 2];  // d_{j0-1+u}, dd_{j0-1+u} = d_{j0+u} - d_{j0-1+u}
 #pragma unroll
-        for (int u = 0; u < 7; ++u) d[u] = ff_sub(s[u + 1], s[u]);
+        for (int u = 0; u < Q + 3; ++u) d[u] = ff_sub(s[u + 1], s[u]);
 #pragma unroll
-        for (int u = 0; u < 6; ++u) dd[u] = ff_sub(d[u + 1], d[u]);
+        for (int u = 0; u < Q + 2; ++u) dd[u] = ff_sub(d[u + 1], d[u]);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < Q; ++k) {
             const int j = j0 + k;
             if (j >= len) break;
             float dh = 0.0f, dl = 0.0f, a = 0.0f, al = 0.0f, e = 0.0f;
@@ -340,6 +373,7 @@ __device__ void tile_begin(const FwdParams &P, MxShared &sh, TileSetup &ts, int6
     ts.u0 = (P.t0 - ts.ti.t0h) * P.inv_dt;
     ts.wlo = INT_MAX;
     ts.whi = INT_MIN;
+    ts.maxbits = 0ull;
     ts.tmax = ((double)(ts.ny / 2) + 1.0) * (double)TAU_UNIT;
     ts.inv_tmax = 1.0 / ts.tmax;
     if (ts.ny > MX_YCAP) {
@@ -459,23 +493,10 @@ __device__ void setup_geometry(const FwdParams &P, TileSetup &ts, int f)
     ts.gnode[i][11 - a] = xc * dr;
 }
 
-// the setup lanes of a tile (see SETUP_PIECE0)
-template <int KIND>
-__device__ __forceinline__ void setup_lanes(const FwdParams &P, TileSetup &ts)
-{
-    const int tid = threadIdx.x;
-    if (tid >= SETUP_PIECE0 && tid < SETUP_PIECE0 + 30)
-        setup_piece<KIND>(P, ts, tid - SETUP_PIECE0);
-    else if (KIND != KIND_TDI && tid >= SETUP_GEO0 && tid < SETUP_GEO0 + 12)
-        setup_geometry(P, ts, tid - SETUP_GEO0);
-}
-
 // cubic through the 4 geometry nodes: monomial coefficients in tau from the Chebyshev
-// inverse Vandermonde (threads FIT0 .. FIT0 + 11)
-__device__ void fit_geometry(const FwdParams &P, const TileSetup &ts, MxShared &sh)
+// inverse Vandermonde (factor f)
+__device__ void fit_geometry(const FwdParams &P, TileSetup &ts, int f)
 {
-    const int f = threadIdx.x - FIT0;
-    if (f < 0 || f >= 12) return;
     double b[4];
     double sc = 1.0;
     for (int k = 0; k < 4; ++k) {
@@ -485,17 +506,33 @@ __device__ void fit_geometry(const FwdParams &P, const TileSetup &ts, MxShared &
         sc *= ts.inv_tmax;
     }
     const ff c0 = ff_from_double(b[0]);
-    sh.g0h[f] = c0.hi;
-    sh.g0l[f] = c0.lo;
-    sh.g1h[f] = (float)b[1];
-    sh.g2[f] = (float)b[2];
-    sh.g3[f] = (float)b[3];
+    ts.g0h[f] = c0.hi;
+    ts.g0l[f] = c0.lo;
+    ts.g1[f] = (float)b[1];
+    ts.g2[f] = (float)b[2];
+    ts.g3[f] = (float)b[3];
+}
+
+// the setup lanes of a tile (see SETUP_PIECE0); warp 7 fits the geometry cubics once its 12
+// lanes have the nodes
+template <int KIND>
+__device__ __forceinline__ void setup_lanes(const FwdParams &P, TileSetup &ts)
+{
+    const int tid = threadIdx.x;
+    if (tid >= SETUP_PIECE0 && tid < SETUP_PIECE0 + 30) {
+        setup_piece<KIND>(P, ts, tid - SETUP_PIECE0);
+    } else if (KIND != KIND_TDI && tid >= SETUP_GEO0 && tid < SETUP_GEO0 + 32) {
+        const int f = tid - SETUP_GEO0;
+        if (f < 12) setup_geometry(P, ts, f);
+        __syncwarp();
+        if (f < 12) fit_geometry(P, ts, f);
+    }
 }
 
 // Reference of each delayed TDI term at the tile centre ic (its chained delay is the sum of the
 // pieces' centre values, exactly what the delay table holds at ic) and the correction weights
 // there with their derivative, interleaved as (U_a, dU_a/deps) pairs (the last 42 threads: in
-// fused launches they run it after their one projection item, beside the others' second).
+// fused launches they have no strain-table item).
 template <int T>
 __device__ void tdi_refs(const FwdParams &P, const TileSetup &ts, MxShared &sh, float *tw)
 {
@@ -883,7 +920,6 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
     if (tid == 0) {
         sh.tot = P.total_tiles >= 0 ? P.total_tiles : P.src.tile_off[P.src.S];
         sh.s_hint = 0;
-        sh.maxbits = 0ull;
     }
     __syncthreads();
     int cur = 0;
@@ -914,8 +950,9 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
             continue;
         }
         const int ny = ts.ny, nb = (int)ts.ti.nb;
-        // ---- stage raw inputs and their maximum; geometry fit; TDI references (TDI-only);
-        //      bookkeeping of the next tile
+        double *pf = reinterpret_cast<double *>(smf + OFF_Y);  // raw strain window (FP64)
+        // ---- raw strain window and its maximum; TDI-only launches: the link series and the
+        //      TDI references
         int wlen = 0;
         long long woff_fx = 0;
         if (KIND != KIND_TDI) {
@@ -925,18 +962,17 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
             if (!wok && tid == 0) atomicOr(P.err, ERR_WINDOW);
             const int woff = wok ? ts.wlo - h - 2 : 0;
             woff_fx = (long long)woff << FX_BITS;
-            double *tmp = reinterpret_cast<double *>(smf + OFF_Y);
             unsigned long long mx = 0ull;
             for (int j = tid; j < wlen; j += blockDim.x) {
                 const int64_t i = ts.k_lo + woff + j;
                 const bool in = i >= 0 && i < ts.ti.nh;
                 const double a = in ? __ldg(ts.ti.hp + i) : 0.0, b = in ? __ldg(ts.ti.hc + i) : 0.0;
-                tmp[j] = a;
-                tmp[MX_WCAP + j] = b;
+                pf[j] = a;
+                pf[MX_WCAP + j] = b;
                 mx = max(mx, max(abs_bits(a), abs_bits(b)));
             }
-            block_absmax(&sh.maxbits, mx);
-            fit_geometry(P, ts, sh);
+            block_absmax(&ts.maxbits, mx);
+            __syncthreads();
         } else {
             double *tmp = reinterpret_cast<double *>(smf + OFF_W);
             unsigned long long mx = 0ull;
@@ -947,53 +983,51 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
                     tmp[l * MX_YCAP + j] = v;
                     mx = max(mx, abs_bits(v));
                 }
-            block_absmax(&sh.maxbits, mx);
+            block_absmax(&ts.maxbits, mx);
             tdi_refs<T>(P, ts, sh, smf + OFF_TW);
+            __syncthreads();
         }
-        if (next && tid == MIXED_THREADS - 1) tile_begin<KIND>(P, sh, tn, gn);
-        __syncthreads();
         // ---- scaled float-float values
         {
-            double scale, unscale;
-            tile_scale(sh.maxbits, scale, unscale);
-            if (tid == 0) sh.unscale = unscale;
-        if (KIND != KIND_TDI) {
-            const double *tmp = reinterpret_cast<const double *>(smf + OFF_Y);
-            for (int j = tid; j < wlen; j += blockDim.x) {
-                const ff a = ff_from_double(tmp[j] * scale), b = ff_from_double(tmp[MX_WCAP + j] * scale);
-                const int p = phw(j);
-                smf[warr(0, A_SHI) + p] = a.hi;
-                smf[warr(0, A_SLO) + p] = a.lo;
-                smf[warr(1, A_SHI) + p] = b.hi;
-                smf[warr(1, A_SLO) + p] = b.lo;
-            }
-        } else {
-            const double *tmp = reinterpret_cast<const double *>(smf + OFF_W);
-            for (int l = 0; l < 6; ++l)
-                for (int j = tid; j < ny; j += blockDim.x) {
-                    const ff v = ff_from_double(tmp[l * MX_YCAP + j] * scale);
-                    smf[ybase(l) + A_SHI * MX_AY + phy(j)] = v.hi;
-                    smf[ybase(l) + A_SLO * MX_AY + phy(j)] = v.lo;
+            const int se = tile_scale_exp(ts.maxbits);
+            if (tid == 0) sh.unscale_e = -se;
+            if (KIND != KIND_TDI) {
+                for (int j = tid; j < wlen; j += blockDim.x) {
+                    const ff a = ff_from_double_scaled(pf[j], se), b = ff_from_double_scaled(pf[MX_WCAP + j], se);
+                    const int p = phw(j);
+                    smf[warr(0, A_SHI) + p] = a.hi;
+                    smf[warr(0, A_SLO) + p] = a.lo;
+                    smf[warr(1, A_SHI) + p] = b.hi;
+                    smf[warr(1, A_SLO) + p] = b.lo;
                 }
-        }
+            } else {
+                const double *tmp = reinterpret_cast<const double *>(smf + OFF_W);
+                for (int l = 0; l < 6; ++l)
+                    for (int j = tid; j < ny; j += blockDim.x) {
+                        const ff v = ff_from_double_scaled(tmp[l * MX_YCAP + j], se);
+                        smf[ybase(l) + A_SHI * MX_AY + phy(j)] = v.hi;
+                        smf[ybase(l) + A_SLO * MX_AY + phy(j)] = v.lo;
+                    }
+            }
         }
         __syncthreads();
-        if (tid == 0) sh.maxbits = 0ull;  // every thread has read it
         long long *Lblk = reinterpret_cast<long long *>(smf + OFF_W);
         float *dLf = smf + OFF_W + 2 * 6 * LB;
         if (KIND != KIND_TDI) {
             // ---- strain difference tables
-            build_tables<true, RLW>(smf, warr(0, A_SHI), MX_AW, 7 * MX_AW, 2, wlen);
+            build_tables<true, RLW, 4>(smf, warr(0, A_SHI), MX_AW, 7 * MX_AW, 2, wlen);
+            if (KIND == KIND_FUSED) tdi_refs<T>(P, ts, sh, smf + OFF_TW);
+            if (next && tid == MIXED_THREADS - 1) tile_begin<KIND>(P, sh, tn, gn);
             __syncthreads();
             // ---- projection reads; then, on the warps with one item: the TDI references and
             //      the next tile's setup
             const int nblk = (ny + PB - 1) / PB;
             for (int it = tid; it < 9 * nblk; it += blockDim.x)
                 proj_item<T>(smf, ts, it / nblk, it % nblk, ny, wlen, woff_fx, P.err);
-            if (KIND == KIND_FUSED) tdi_refs<T>(P, ts, sh, smf + OFF_TW);
             if (next && tn.ti.ok && tn.ti.nb > 0) setup_lanes<KIND>(P, tn);
             __syncthreads();
-            // ---- link series (in place over the staged reads)
+            // ---- link series, in place over the staged reads: one thread per sample reads all
+            //      of the sample's staged reads before writing its six links (same column)
             for (int j = tid; j < ny; j += blockDim.x) {
                 const int ai = phy(j);
                 ff rp[3], rc[3];
@@ -1010,15 +1044,19 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
                     const ff ep = {smf[OFF_Y + (4 * rd + 0) * MX_AY + ai], smf[OFF_Y + (4 * rd + 1) * MX_AY + ai]};
                     const ff ec = {smf[OFF_Y + (4 * rd + 2) * MX_AY + ai], smf[OFF_Y + (4 * rd + 3) * MX_AY + ai]};
                     const int r = l < 3 ? l : (l == 3 ? 0 : (l == 4 ? 2 : 1));  // receiving spacecraft
-                    y[l] = ff_add(ff_mul(geom_at(sh, l, tau), ff_sub(ep, rp[r])),
-                                  ff_mul(geom_at(sh, 6 + l, tau), ff_sub(ec, rc[r])));
+                    const ff dp = ff_sub(ep, rp[r]), dc = ff_sub(ec, rc[r]);
+                    // c(tau) = c0 + v(tau): c0 in float-float, v (at most 1e-4 of c0) in FP32
+                    const float vp = tau * fmaf(tau, fmaf(tau, ts.g3[l], ts.g2[l]), ts.g1[l]);
+                    const float vc = tau * fmaf(tau, fmaf(tau, ts.g3[6 + l], ts.g2[6 + l]), ts.g1[6 + l]);
+                    const ff yl = ff_add(ff_mul({ts.g0h[l], ts.g0l[l]}, dp), ff_mul({ts.g0h[6 + l], ts.g0l[6 + l]}, dc));
+                    y[l] = ff_add_f(yl, fmaf(vp, dp.hi, vc * dc.hi));
                 }
                 const int64_t k = ts.k_lo + j;
                 if (KIND == KIND_PROJECT) {
                     double *o = ts.ti.out;
                     const int64_t N = ts.ti.N;
 #pragma unroll
-                    for (int l = 0; l < 6; ++l) o[l * N + k] = ff_to_double(y[l]) * sh.unscale;
+                    for (int l = 0; l < 6; ++l) o[l * N + k] = ff2d_scaled(y[l].hi, y[l].lo, sh.unscale_e);
                 } else {
                     const bool in = k >= 0 && k < ts.ti.N;
 #pragma unroll
@@ -1042,7 +1080,7 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
             }
             __syncthreads();
             // ---- link difference tables
-            build_tables<false, RLY>(smf, ybase(0), MX_AY, 6 * MX_AY, 6, ny);
+            build_tables<false, RLY, 5>(smf, ybase(0), MX_AY, 6 * MX_AY, 6, ny);
             __syncthreads();
             // ---- X, Y, Z
             const int nbb = (nb + TB - 1) / TB;
@@ -1057,7 +1095,7 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
                 double *o = ts.ti.out + ch * ts.ti.N + ts.ti.n0 + i0;
 #pragma unroll
                 for (int k = 0; k < TB; ++k)
-                    if (k < kmax) o[k] = ((double)hi[k] + (double)(lo[k] + sm[k])) * sh.unscale;
+                    if (k < kmax) o[k] = ff2d_scaled(hi[k], lo[k] + sm[k], sh.unscale_e);
             }
         }
         __syncthreads();

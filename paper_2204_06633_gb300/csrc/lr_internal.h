@@ -129,6 +129,7 @@ constexpr int MX_AW = 8 * mx_rl(MX_WCAP);  // floats per strain-window array
 constexpr int MX_TDI_BLOCK = 4;            // consecutive outputs per TDI work item
 // correction-weight pairs (U, dU/deps) per TDI term, padded to a multiple of 2 pairs
 __host__ __device__ constexpr int mx_nup(int T) { return T >= 4 ? ((T - 3 + 1) & ~1) : 2; }
+// strain tables, link tables, TDI weights
 __host__ __device__ constexpr int mx_smem_floats(int T) { return 14 * MX_AW + 36 * MX_AY + 42 * 2 * mx_nup(T); }
 // largest tile the mixed kernels stage: the link span within MX_YCAP, the strain window
 // (span + read spread 2 lproj_b + T + 6) within MX_WCAP, TDI items (3 channels x tile/4) in
