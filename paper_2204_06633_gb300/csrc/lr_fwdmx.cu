@@ -106,7 +106,7 @@ struct TileSetup {
     // in tau (constant in float-float)
     double gnode[4][12];
     double tmax, inv_tmax;
-    float g0h[12], g0l[12], g1[12], g2[12], g3[12];
+    float g0h[12], g0l[12], g1h[12], g1l[12], g2[12], g3[12];
     // maximum of the tile's raw inputs (bit pattern)
     unsigned long long maxbits;
 };
@@ -239,6 +239,21 @@ __device__ inline void mx_tile(const FwdParams &P, int64_t g, int ochan, int64_t
 }
 
 
+// value of a fitted geometry factor at tau: constant and linear term in float-float (near a sky
+// direction along an arm 1/(1 - k.n) changes by a large fraction over one tile), the quadratic
+// and cubic terms in FP32
+__device__ __forceinline__ ff geom_at(const TileSetup &ts, int f, float tau)
+{
+    // g0 + g1 tau: exact product of the high parts, one two_sum; every lower-order piece (the
+    // low parts, the product's rounding error, the FP32 quadratic and cubic terms) gathered in
+    // the low word (an unnormalised pair, which the float-float product that follows accepts)
+    const float p = ts.g1h[f] * tau;
+    const float pe = fmaf(ts.g1h[f], tau, -p);
+    const ff s = two_sum(ts.g0h[f], p);
+    const float q = tau * tau * fmaf(tau, ts.g3[f], ts.g2[f]);
+    return {s.hi, s.lo + (fmaf(ts.g1l[f], tau, ts.g0l[f]) + (pe + q))};
+}
+
 // block max of the bit patterns b of |v| (for non-negative doubles the order of the patterns is
 // the order of the values; a NaN orders above every finite value)
 __device__ __forceinline__ unsigned long long abs_bits(double v)
@@ -264,10 +279,11 @@ __device__ __forceinline__ int tile_scale_exp(unsigned long long maxbits)
     return eb >= 1 && eb <= 2044 ? 1022 - eb : 0;
 }
 
-// x 2^se as float-float by integer work on the bit pattern: hi holds x's 24 leading significand
-// bits (truncated) with the exponent moved by se, lo the remaining 29 bits rounded to FP32.
-// Values whose scaled hi falls below the FP32 normal range read as zero (below 2^-126 of the
-// scaled tile maximum); an infinity or NaN passes through in hi.
+// x 2^se as float-float by integer work on the bit pattern: hi is x's significand rounded to 24
+// bits (a carry out of the significand rolls into the exponent field) with the exponent moved by
+// se, lo the signed remainder (at most 2^28 units of x's last place, so |lo| <= ulp(hi)/2) as
+// FP32.  Values whose scaled hi falls below the FP32 normal range read as zero (below 2^-126 of
+// the scaled tile maximum); an infinity or NaN passes through in hi.
 __device__ __forceinline__ ff ff_from_double_scaled(double x, int se)
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -277,13 +293,14 @@ __device__ __forceinline__ ff ff_from_double_scaled(double x, int se)
     if (ex == 0x7ff) return {__uint_as_float(sg | 0x7f800000u | (m ? 0x400000u : 0u)), 0.0f};
     const int eh = ex - 896 + se;  // FP32 biased exponent of hi (1023 - 127 = 896)
     if (ex == 0 || eh <= 0) return {__uint_as_float(sg), 0.0f};
-    if (eh >= 255) return {__uint_as_float(sg | 0x7f800000u), 0.0f};
-    const float hi = __uint_as_float(sg | ((unsigned)eh << 23) | (unsigned)(m >> 29));
-    // remainder r 2^(eh - 127 - 52); zero once that power leaves the normal range (2^-75 of
-    // the scaled maximum at most)
-    const unsigned r = (unsigned)(m & 0x1fffffffu);
+    if (eh >= 254) return {__uint_as_float(sg | 0x7f800000u), 0.0f};
+    const unsigned long long t = m + (1ull << 28);  // round the significand at its 29th bit
+    const float hi = __uint_as_float(sg | (((unsigned)eh << 23) + (unsigned)(t >> 29)));
+    // remainder r 2^(eh - 127 - 52), r in [-2^28, 2^28); zero once that power leaves the normal
+    // range (2^-75 of the scaled maximum at most)
+    const int r = (int)((long long)m - (long long)((t >> 29) << 29));
     const int el = eh - 52;
-    const float lo = el > 0 ? __uint2float_rn(r) * __uint_as_float((unsigned)el << 23) : 0.0f;
+    const float lo = el > 0 ? __int2float_rn(r) * __uint_as_float((unsigned)el << 23) : 0.0f;
     return {hi, sg ? -lo : lo};
 }
 
@@ -505,10 +522,11 @@ __device__ void fit_geometry(const FwdParams &P, TileSetup &ts, int f)
         b[k] = acc * sc;
         sc *= ts.inv_tmax;
     }
-    const ff c0 = ff_from_double(b[0]);
+    const ff c0 = ff_from_double(b[0]), c1 = ff_from_double(b[1]);
     ts.g0h[f] = c0.hi;
     ts.g0l[f] = c0.lo;
-    ts.g1[f] = (float)b[1];
+    ts.g1h[f] = c1.hi;
+    ts.g1l[f] = c1.lo;
     ts.g2[f] = (float)b[2];
     ts.g3[f] = (float)b[3];
 }
@@ -1044,12 +1062,8 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
                     const ff ep = {smf[OFF_Y + (4 * rd + 0) * MX_AY + ai], smf[OFF_Y + (4 * rd + 1) * MX_AY + ai]};
                     const ff ec = {smf[OFF_Y + (4 * rd + 2) * MX_AY + ai], smf[OFF_Y + (4 * rd + 3) * MX_AY + ai]};
                     const int r = l < 3 ? l : (l == 3 ? 0 : (l == 4 ? 2 : 1));  // receiving spacecraft
-                    const ff dp = ff_sub(ep, rp[r]), dc = ff_sub(ec, rc[r]);
-                    // c(tau) = c0 + v(tau): c0 in float-float, v (at most 1e-4 of c0) in FP32
-                    const float vp = tau * fmaf(tau, fmaf(tau, ts.g3[l], ts.g2[l]), ts.g1[l]);
-                    const float vc = tau * fmaf(tau, fmaf(tau, ts.g3[6 + l], ts.g2[6 + l]), ts.g1[6 + l]);
-                    const ff yl = ff_add(ff_mul({ts.g0h[l], ts.g0l[l]}, dp), ff_mul({ts.g0h[6 + l], ts.g0l[6 + l]}, dc));
-                    y[l] = ff_add_f(yl, fmaf(vp, dp.hi, vc * dc.hi));
+                    y[l] = ff_add(ff_mul(geom_at(ts, l, tau), ff_sub(ep, rp[r])),
+                                  ff_mul(geom_at(ts, 6 + l, tau), ff_sub(ec, rc[r])));
                 }
                 const int64_t k = ts.k_lo + j;
                 if (KIND == KIND_PROJECT) {

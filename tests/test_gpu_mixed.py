@@ -79,6 +79,24 @@ def test_small_and_ragged(ctx, orbits, N, tile):
     mixed(ctx, src, N, 25, orbits["flex"], tile=tile)
 
 
+def test_sky_along_an_arm(ctx, orbits):
+    """Sky direction 1.4e-3 rad from arm 12 at mid-span on the flexing orbit: 1/(2(1 - k.n)) and
+    the patterns then change by a large fraction over one tile, which the tile's geometry cubic
+    must carry at float-float accuracy."""
+    N = 20000
+    orb = orbits["flex"].orb
+    tm = 0.5 * N * DT
+    x = np.array([[np.interp(tm, orb.t_knots, orb.pos[s, d]) for d in range(3)] for s in range(3)])
+    n12 = (x[0] - x[1]) / np.linalg.norm(x[0] - x[1])
+    perp = np.cross(n12, [0.0, 0.0, 1.0])
+    perp /= np.linalg.norm(perp)
+    k = np.cos(1.4e-3) * n12 + np.sin(1.4e-3) * perp  # propagation direction; e_r = -k
+    lam, beta = float(np.arctan2(-k[1], -k[0])), float(np.arcsin(-k[2]))
+    for f in (1e-4, 3e-3):
+        src = synth.Source(A=1e-21, f=f, fdot=0.0, phi0=0.3, iota=0.7, psi=0.2, lam=lam, beta=beta)
+        mixed(ctx, src, N, 25, orbits["flex"])
+
+
 def test_tile_beyond_staging_capacity_is_refused(ctx, orbits):
     """A mixed tile whose link span would not fit the shared-memory arrays is a range error."""
     with pytest.raises(lr.LRError) as e:
