@@ -87,7 +87,9 @@ typedef struct {
     int64_t n;            /* output length of the single-source calls (>= 1) */
     const lr_orbit *proj_orbit;  /* positions + delays used by the projection */
     const lr_orbit *tdi_orbit;   /* delays used by TDI; may differ (hybrid templates) */
-    int tile;             /* output samples per CTA tile; 0 = autotuned / default */
+    int tile;             /* output samples per CTA tile; 0 = default.  Mixed plans stage a tile in
+                             fixed shared-memory arrays: at most 340 outputs at order 25 and dt =
+                             10 s (less for longer TDI halos); a larger tile is LR_ERR_RANGE */
     int threads;          /* threads per CTA; 0 = default */
 } lr_plan_desc;
 
@@ -170,7 +172,7 @@ LR_API int lr_response_batched(lr_plan *plan, int64_t S, const int64_t *h_off, c
                                double *xyz, void *stream);
 /* ------------------------------------------------------------------ graphs and tuning */
 typedef struct lr_graph lr_graph;
-/* Captures one lr_response_batched call (tile-table kernel + persistent fused kernel) into an
+/* Captures one lr_response_batched call (batch-table kernels + persistent fused kernel) into an
  * instantiated CUDA graph.  The plan's batch workspace is reserved before the capture; the graph
  * keeps the given device pointers: rewrite the inputs in place between replays.  The batch
  * shape (S, offsets) must not change while the graph is used.  Owned by the caller. */
@@ -187,18 +189,19 @@ LR_API int lr_graph_destroy(lr_graph *graph);
 LR_API int lr_plan_autotune(lr_plan *plan, int64_t n_samples, int use_cache, void *stream, int *tile_out);
 
 /* Batched forward that allocates no device memory.  Same arguments, results and asynchrony as
- * lr_response_batched, which allocates its per-batch tile table on first use; this variant keeps
- * that table in a fixed device array inside the library, for callers that may not allocate device
+ * lr_response_batched, which allocates its per-batch tables on first use; this variant keeps
+ * them in fixed device arrays inside the library, for callers that may not allocate device
  * memory once their run has started (a sampler or service that has budgeted all device memory
  * up front, or that cannot take the device-wide synchronisation of cudaMalloc / cudaFree).
  * The paper has no counterpart: it is an allocation policy of this library.
  *   S <= LR_NOALLOC_MAX_SOURCES, else LR_ERR_RANGE (nothing is launched).
- *   The array (8 * (LR_NOALLOC_MAX_SOURCES + 1) bytes) is held by every GPU that loads the
- *   library until the process exits, and is shared by every call on that GPU: each call rewrites
- *   the entries it uses before reading them, and calls that overlap on the GPU (other streams,
- *   other threads, other plans) race on it.  The first call on a device looks up the array's
- *   device address (cudaGetSymbolAddress, with that device made current for the look-up); make
- *   that first call before any stream capture. */
+ *   The arrays (the tile table, 8 * (LR_NOALLOC_MAX_SOURCES + 1) bytes, and the sources' sky
+ *   frames, 88 * LR_NOALLOC_MAX_SOURCES bytes) are held by every GPU that loads the library until
+ *   the process exits, and are shared by every call on that GPU: each call rewrites the entries
+ *   it uses before reading them, and calls that overlap on the GPU (other streams, other threads,
+ *   other plans) race on them.  The first call on a device looks up the arrays' device addresses
+ *   (cudaGetSymbolAddress, with that device made current for the look-up); make that first call
+ *   before any stream capture. */
 #define LR_NOALLOC_MAX_SOURCES 65536
 LR_API int lr_response_batched_noalloc(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
                                        const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
