@@ -170,6 +170,23 @@ LR_API int lr_backward(lr_plan *plan, const double *hp, const double *hc, int64_
 LR_API int lr_response_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
                                const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
                                double *xyz, void *stream);
+/* Batched forward on HOST buffers: the same arguments and results as lr_response_batched, but
+ * h_off, out_off, t0_h, sky, hp, hc and xyz are host arrays (h_off[0] = out_off[0] = 0, both
+ * non-decreasing).  The batch is cut into chunks of whole sources (about 2^25 outputs each) and
+ * (LR_PIPELINE_CHUNK_OUTPUTS in the environment overrides the chunk size)
+ * the copy-in of one chunk, the fused kernel on the previous one and the copy-out of the one
+ * before run concurrently on three library streams, in two plan-owned device slots (allocated on
+ * first use and grown when a larger chunk arrives; freed with the plan).  Work queued earlier on
+ * `stream` is waited for; the call returns when every result is in xyz (synchronous).  hp, hc and
+ * xyz should be page-locked (cudaHostAlloc / cudaHostRegister) for the copies to overlap; pageable
+ * memory gives the same results with serialised copies.  The paper's method is unchanged: this
+ * is the library's transfer schedule for data that lives in host memory.
+ * Errors: LR_ERR_INVALID_ARG for null pointers, S < 1 or non-monotone offsets, LR_ERR_RANGE for
+ * S > 2^24, LR_ERR_OOM / LR_ERR_CUDA as elsewhere; device-detected faults are read with
+ * lr_plan_check. */
+LR_API int lr_response_batched_host(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
+                                    const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
+                                    double *xyz, void *stream);
 /* ------------------------------------------------------------------ graphs and tuning */
 typedef struct lr_graph lr_graph;
 /* Captures one lr_response_batched call (batch-table kernels + persistent fused kernel) into an

@@ -11,6 +11,7 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -66,6 +67,7 @@ _SIGS = {
     "lr_response_batched": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
     "lr_backward_batched": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "lr_response_batched_noalloc": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "lr_response_batched_host": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
     "lr_response_batched_graph": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _PP]),
     "lr_graph_launch": (_I, [_P, _P]),
     "lr_graph_destroy": (_I, [_P]),
@@ -127,6 +129,24 @@ def _devi64(t: torch.Tensor, name: str, numel: int) -> int:
     return t.data_ptr()
 
 
+def _host(a, dtype, name: str, numel: int | None = None):
+    """(pointer, keep-alive object) of a contiguous host array: a CPU torch tensor (pinned or not)
+    or anything numpy can view; numpy inputs are converted (copied) only when they must be."""
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda:
+            raise TypeError(f"{name} must be a host (CPU) array")
+        want = torch.float64 if dtype == np.float64 else torch.int64
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous {want} CPU tensor")
+        if numel is not None and a.numel() != numel:
+            raise ValueError(f"{name} has {a.numel()} elements, expected {numel}")
+        return a.data_ptr(), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    if numel is not None and arr.size != numel:
+        raise ValueError(f"{name} has {arr.size} elements, expected {numel}")
+    return arr.ctypes.data, arr
+
+
 def _sky(sky) -> lr_sky:
     if isinstance(sky, lr_sky):
         return sky
@@ -156,7 +176,6 @@ class Orbit:
     or None for the Newtonian light-time solve done by the library."""
 
     def __init__(self, ctx: Context, t_knots, pos, delays=None, bc: int = NOT_A_KNOT):
-        import numpy as np
         self.ctx = ctx
         self._tk = np.ascontiguousarray(t_knots, dtype=np.float64)
         self._pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(9, -1)
@@ -172,7 +191,6 @@ class Orbit:
         return self._h
 
     def delays_at_knots(self):
-        import numpy as np
         out = np.empty((6, len(self._tk)))
         _check("lr_orbit_delays", library().lr_orbit_delays(self._h, out.ctypes.data, len(self._tk)))
         return out
@@ -262,6 +280,27 @@ class Plan:
             self._h, S, _devi64(h_off, "h_off", S + 1), _devi64(out_off, "out_off", S + 1), _dev64(t0h, "t0h", S),
             _dev64(sky, "sky", 3 * S), _dev64(hp, "hp"), _dev64(hc, "hc", hp.numel()), _dev64(xyz, "xyz"),
             _stream_handle(stream)))
+        return xyz
+
+    def response_batched_host(self, h_off, out_off, t0h, sky, hp, hc, xyz=None, stream=None):
+        """The batched response on host arrays (numpy or CPU tensors; page-locked tensors let
+        the copies overlap the kernels): chunks of sources are copied in, computed and copied
+        out concurrently.  Synchronous; returns xyz (host, float64 [3 * out_off[-1]])."""
+        S = len(t0h)
+        ho, _k1 = _host(h_off, np.int64, "h_off", S + 1)
+        oo, _k2 = _host(out_off, np.int64, "out_off", S + 1)
+        total = int(out_off[-1])
+        if xyz is None:
+            xyz = np.empty(3 * total)
+        xo, _k3 = _host(xyz, np.float64, "xyz", 3 * total)
+        if isinstance(xyz, np.ndarray) and xo != xyz.ctypes.data:
+            raise ValueError("xyz must be a contiguous float64 array")
+        t0, _k4 = _host(t0h, np.float64, "t0h", S)
+        sk, _k5 = _host(sky, np.float64, "sky", 3 * S)
+        hpp, _k6 = _host(hp, np.float64, "hp")
+        hcp, _k7 = _host(hc, np.float64, "hc", len(hp) if not isinstance(hp, torch.Tensor) else hp.numel())
+        _check("lr_response_batched_host", library().lr_response_batched_host(
+            self._h, S, ho, oo, t0, sk, hpp, hcp, xo, _stream_handle(stream)))
         return xyz
 
     def autotune(self, n_samples: int, use_cache: bool = True, stream=None) -> int:

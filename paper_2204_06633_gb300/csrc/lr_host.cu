@@ -12,6 +12,7 @@
 #include "lr_internal.h"
 #include "lr_bwd.h"
 #include "lr_launch.h"
+#include "lr_pipeline.h"
 #include "lr_planview.h"
 
 struct lr_ctx {
@@ -49,6 +50,8 @@ struct lr_plan {
     int64_t partial_cap;
     int64_t *d_ktile_off, *d_htile_off;
     int64_t ktile_cap;
+    // host-buffer pipeline (lr_response_batched_host), created on first use
+    lr::PipeWork *pipe;
 };
 
 namespace lr {
@@ -432,6 +435,7 @@ LR_API int lr_plan_create(lr_ctx *ctx, const lr_plan_desc *d, lr_plan **out)
     p->partial_cap = 0;
     p->d_ktile_off = p->d_htile_off = nullptr;
     p->ktile_cap = 0;
+    p->pipe = nullptr;
     lr::FwdParams &P = p->base;
     std::memset(&P, 0, sizeof(P));
     P.dt = d->dt;
@@ -506,6 +510,7 @@ LR_API int lr_plan_destroy(lr_plan *plan)
     if (plan->d_partial) cudaFree(plan->d_partial);
     if (plan->d_ktile_off) cudaFree(plan->d_ktile_off);
     if (plan->d_htile_off) cudaFree(plan->d_htile_off);
+    lr::pipe_free(plan->pipe);
     delete plan;
     return LR_OK;
 }
@@ -813,6 +818,8 @@ int plan_reserve_batch(lr_plan *plan, int64_t S)
     plan->tile_cap = S + 1;
     return LR_OK;
 }
+
+PipeWork *&plan_pipe(lr_plan *plan) { return plan->pipe; }
 
 SkyConst *plan_sky_table(lr_plan *plan) { return reinterpret_cast<SkyConst *>(plan->d_tile_off + plan->tile_cap); }
 
