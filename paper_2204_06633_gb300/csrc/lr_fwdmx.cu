@@ -712,7 +712,7 @@ __device__ __forceinline__ void proj_item(float *smf, const TileSetup &sh, int r
 #pragma unroll
         for (int a = 0; a < NU; ++a) W[a] = f2pack(U0[a], U1[a]);
     }
-#pragma unroll
+#pragma unroll 1
     for (int pol = 0; pol < 2; ++pol) {
         float C[PB];
         if constexpr (T >= 4) {
@@ -803,17 +803,16 @@ __device__ __noinline__ void tdi_read_exact(const float *smf, int lk, int m, flo
     out[5] = C;
 }
 
-// Chain c (sign SG) of channel ch for the outputs of item b (i0 = 4 b; nl = output index in
-// the span).  The chained delay of the item's first output is carried in 64-bit fixed point
+// Chain c of channel ch, added to the accumulators, for the outputs of item b (i0 = 4 b;
+// nl = output index in the span).  The chained delay of the item's first output is carried in 64-bit fixed point
 // and split once per term; the other outputs differ from it by the exact FP32 increments
 // dk, so output k reads at index m0 + k with fraction eh + (el - dk 2^-44) while that stays
 // in [0, 1).
-template <int T, int SG>
+template <int T>
 __device__ __forceinline__ void tdi_chain(const FwdParams &P, const MxShared &sh, int ny, const float *smf,
-                                          const long long *Lblk, const float *dLf, int ch, int b, int kmax,
+                                          const long long *Lblk, const float *dLf, int ch, int c, int b, int kmax,
                                           float *hi, float *lo, float *sm)
 {
-    constexpr int c = SG > 0 ? 0 : 1;
     constexpr int h = (T - 2) / 2;
     constexpr int NU = T >= 4 ? T - 3 : 1;
     constexpr int NE = NU + TB - 1;
@@ -826,9 +825,9 @@ __device__ __forceinline__ void tdi_chain(const FwdParams &P, const MxShared &sh
         for (int k = 0; k < TB; ++k) {
             const int ai = phy(nl0 + k);
             const float shi = smf[yb + A_SHI * MX_AY + ai], slo = smf[yb + A_SLO * MX_AY + ai];
-            const ff t = two_sum(hi[k], SG > 0 ? shi : -shi);
+            const ff t = two_sum(hi[k], shi);
             hi[k] = t.hi;
-            lo[k] += (SG > 0 ? slo : -slo) + t.lo;
+            lo[k] += slo + t.lo;
         }
     }
     long long D0 = 0;
@@ -905,7 +904,7 @@ __device__ __forceinline__ void tdi_chain(const FwdParams &P, const MxShared &sh
 #pragma unroll
             for (int k = 0; k < TB; ++k) {
                 const int ai = o[(h + k) & 7] + ((h + k) >> 3);
-                acc_term<SG, T>(hi[k], lo[k], sm[k], smf[yb + A_SHI * MX_AY + ai], smf[yb + A_SLO * MX_AY + ai],
+                acc_term<1, T>(hi[k], lo[k], sm[k], smf[yb + A_SHI * MX_AY + ai], smf[yb + A_SLO * MX_AY + ai],
                                 smf[yb + A_DHI * MX_AY + ai], smf[yb + A_DLO * MX_AY + ai],
                                 smf[yb + A_A * MX_AY + ai], eh, el[k], q0, g, C[k]);
             }
@@ -916,7 +915,7 @@ __device__ __forceinline__ void tdi_chain(const FwdParams &P, const MxShared &sh
                     const Split sk = split_fx(((long long)(nl0 + k) << FX_BITS) - (D0 + (long long)dk[k]));
                     float r[6];
                     tdi_read_exact<T>(smf, lk, sk.m, sk.ehi, sk.elo, ny, P.err, r);
-                    acc_term<SG, T>(hi[k], lo[k], sm[k], r[0], r[1], r[2], r[3], r[4], sk.ehi, sk.elo,
+                    acc_term<1, T>(hi[k], lo[k], sm[k], r[0], r[1], r[2], r[3], r[4], sk.ehi, sk.elo,
                                     sk.ehi * (sk.ehi - 1.0f), 2.0f * sk.ehi - 1.0f, r[5]);
                 }
             }
@@ -1104,8 +1103,17 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
                 float hi[TB], lo[TB], sm[TB];
 #pragma unroll
                 for (int k = 0; k < TB; ++k) hi[k] = lo[k] = sm[k] = 0.0f;
-                tdi_chain<T, 1>(P, sh, ny, smf, Lblk, dLf, ch, b, kmax, hi, lo, sm);
-                tdi_chain<T, -1>(P, sh, ny, smf, Lblk, dLf, ch, b, kmax, hi, lo, sm);
+                // X = A - B = -((-A) + B): both chains through one code copy
+#pragma unroll 1
+                for (int c = 0; c < 2; ++c) {
+                    tdi_chain<T>(P, sh, ny, smf, Lblk, dLf, ch, c, b, kmax, hi, lo, sm);
+#pragma unroll
+                    for (int k = 0; k < TB; ++k) {
+                        hi[k] = -hi[k];
+                        lo[k] = -lo[k];
+                        sm[k] = -sm[k];
+                    }
+                }
                 double *o = ts.ti.out + ch * ts.ti.N + ts.ti.n0 + i0;
 #pragma unroll
                 for (int k = 0; k < TB; ++k)
