@@ -74,6 +74,39 @@ __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsign
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
 }
+
+__device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ unsigned long long fsub2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ unsigned long long fmul2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// both lanes negated (sign bits flipped)
+__device__ __forceinline__ unsigned long long fneg2(unsigned long long a) { return a ^ 0x8000000080000000ull; }
+
+// two_sum on both lanes of packed pairs (each lane exactly the scalar two_sum)
+__device__ __forceinline__ void two_sum2(unsigned long long a, unsigned long long b, unsigned long long &s,
+                                         unsigned long long &e)
+{
+    s = fadd2(a, b);
+    const unsigned long long bb = fsub2(s, a);
+    e = fadd2(fsub2(a, fsub2(s, bb)), fsub2(b, bb));
+}
 enum { A_SHI = 0, A_SLO, A_DHI, A_DLO, A_A, A_E, A_ALO };
 
 __device__ __forceinline__ int phw(int j) { return (j & 7) * RLW + (j >> 3); }
@@ -774,6 +807,42 @@ __device__ __forceinline__ void acc_term(float &hi, float &lo, float &sm, float 
     }
 }
 
+// acc_term<1, T> on a pair of outputs at once (packed lanes, each lane the same IEEE operations
+// as the scalar form): EH, NEH (= -eh), G, Q0 broadcast; EL, NC (= -C) and the loaded values per
+// output
+template <int T>
+__device__ __forceinline__ void acc_term2(unsigned long long &HI, unsigned long long &LO, unsigned long long &SM,
+                                          unsigned long long SHI, unsigned long long SLO, unsigned long long DHI,
+                                          unsigned long long DLO, unsigned long long A, unsigned long long EH,
+                                          unsigned long long NEH, unsigned long long EL, unsigned long long G,
+                                          unsigned long long Q0, unsigned long long NC)
+{
+    const unsigned long long Pp = fmul2(EH, DHI);
+    const unsigned long long NPE = ffma2(NEH, DHI, Pp);  // -(eh dhi - p) exactly rounded: -pe
+    unsigned long long S1, E1, S2, E2;
+    two_sum2(HI, SHI, S1, E1);
+    two_sum2(S1, Pp, S2, E2);
+    HI = S2;
+    const unsigned long long X = ffma2(EH, DLO, fmul2(EL, DHI));
+    const unsigned long long L = fadd2(SLO, fsub2(X, NPE));
+    LO = fadd2(LO, fadd2(L, fadd2(E1, E2)));
+    if constexpr (T >= 4) SM = fadd2(SM, ffma2(ffma2(EL, G, Q0), A, NC));
+}
+
+__device__ __forceinline__ float lane(unsigned long long v, int k)
+{
+    float a, b;
+    f2unpack(v, a, b);
+    return k ? b : a;
+}
+
+__device__ __forceinline__ void set_lane(unsigned long long &v, int k, float x)
+{
+    float a, b;
+    f2unpack(v, a, b);
+    v = k ? f2pack(a, x) : f2pack(x, b);
+}
+
 // one delayed read of link lk with exact weights (the rare reads off the tile reference);
 // an out-of-window stencil reads 0 and records ERR_WINDOW
 template <int T>
@@ -811,7 +880,7 @@ __device__ __noinline__ void tdi_read_exact(const float *smf, int lk, int m, flo
 template <int T>
 __device__ __forceinline__ void tdi_chain(const FwdParams &P, const MxShared &sh, int ny, const float *smf,
                                           const long long *Lblk, const float *dLf, int ch, int c, int b, int kmax,
-                                          float *hi, float *lo, float *sm)
+                                          unsigned long long *HI, unsigned long long *LO, unsigned long long *SM)
 {
     constexpr int h = (T - 2) / 2;
     constexpr int NU = T >= 4 ? T - 3 : 1;
@@ -822,12 +891,14 @@ __device__ __forceinline__ void tdi_chain(const FwdParams &P, const MxShared &sh
     {
         const int yb = ybase(c_tdimx.link[ch][c][0]);
 #pragma unroll
-        for (int k = 0; k < TB; ++k) {
-            const int ai = phy(nl0 + k);
-            const float shi = smf[yb + A_SHI * MX_AY + ai], slo = smf[yb + A_SLO * MX_AY + ai];
-            const ff t = two_sum(hi[k], shi);
-            hi[k] = t.hi;
-            lo[k] += slo + t.lo;
+        for (int pr = 0; pr < TB / 2; ++pr) {
+            const int a0 = phy(nl0 + 2 * pr), a1 = phy(nl0 + 2 * pr + 1);
+            const unsigned long long SHI = f2pack(smf[yb + A_SHI * MX_AY + a0], smf[yb + A_SHI * MX_AY + a1]);
+            const unsigned long long SLO = f2pack(smf[yb + A_SLO * MX_AY + a0], smf[yb + A_SLO * MX_AY + a1]);
+            unsigned long long S, E;
+            two_sum2(HI[pr], SHI, S, E);
+            HI[pr] = S;
+            LO[pr] = fadd2(LO[pr], fadd2(SLO, E));
         }
     }
     long long D0 = 0;
@@ -901,12 +972,15 @@ __device__ __forceinline__ void tdi_chain(const FwdParams &P, const MxShared &sh
                     C[k] = fmaf(dref + el[k], c1, c0);
                 }
             }
+            const unsigned long long EH = f2pack(eh, eh), NEH = f2pack(-eh, -eh);
+            const unsigned long long G2 = f2pack(g, g), Q02 = f2pack(q0, q0);
 #pragma unroll
-            for (int k = 0; k < TB; ++k) {
-                const int ai = o[(h + k) & 7] + ((h + k) >> 3);
-                acc_term<1, T>(hi[k], lo[k], sm[k], smf[yb + A_SHI * MX_AY + ai], smf[yb + A_SLO * MX_AY + ai],
-                                smf[yb + A_DHI * MX_AY + ai], smf[yb + A_DLO * MX_AY + ai],
-                                smf[yb + A_A * MX_AY + ai], eh, el[k], q0, g, C[k]);
+            for (int pr = 0; pr < TB / 2; ++pr) {
+                const int k0 = 2 * pr, k1 = 2 * pr + 1;
+                const int a0 = o[(h + k0) & 7] + ((h + k0) >> 3), a1 = o[(h + k1) & 7] + ((h + k1) >> 3);
+                auto ld = [&](int arr) { return f2pack(smf[yb + arr * MX_AY + a0], smf[yb + arr * MX_AY + a1]); };
+                acc_term2<T>(HI[pr], LO[pr], SM[pr], ld(A_SHI), ld(A_SLO), ld(A_DHI), ld(A_DLO), ld(A_A), EH, NEH,
+                             f2pack(el[k0], el[k1]), G2, Q02, f2pack(-C[k0], -C[k1]));
             }
         } else {
 #pragma unroll
@@ -915,8 +989,12 @@ __device__ __forceinline__ void tdi_chain(const FwdParams &P, const MxShared &sh
                     const Split sk = split_fx(((long long)(nl0 + k) << FX_BITS) - (D0 + (long long)dk[k]));
                     float r[6];
                     tdi_read_exact<T>(smf, lk, sk.m, sk.ehi, sk.elo, ny, P.err, r);
-                    acc_term<1, T>(hi[k], lo[k], sm[k], r[0], r[1], r[2], r[3], r[4], sk.ehi, sk.elo,
-                                    sk.ehi * (sk.ehi - 1.0f), 2.0f * sk.ehi - 1.0f, r[5]);
+                    float hk = lane(HI[k >> 1], k & 1), lk_ = lane(LO[k >> 1], k & 1), sk_ = lane(SM[k >> 1], k & 1);
+                    acc_term<1, T>(hk, lk_, sk_, r[0], r[1], r[2], r[3], r[4], sk.ehi, sk.elo,
+                                   sk.ehi * (sk.ehi - 1.0f), 2.0f * sk.ehi - 1.0f, r[5]);
+                    set_lane(HI[k >> 1], k & 1, hk);
+                    set_lane(LO[k >> 1], k & 1, lk_);
+                    set_lane(SM[k >> 1], k & 1, sk_);
                 }
             }
         }
@@ -1100,24 +1178,27 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
             for (int it = tid; it < 3 * nbb; it += blockDim.x) {
                 const int ch = it / nbb, b = it - ch * nbb, i0 = TB * b;
                 const int kmax = min(TB, nb - i0);
-                float hi[TB], lo[TB], sm[TB];
+                // float-float accumulators (hi, lo) and the FP32 small terms, packed over output pairs
+                unsigned long long HI[TB / 2], LO[TB / 2], SM[TB / 2];
 #pragma unroll
-                for (int k = 0; k < TB; ++k) hi[k] = lo[k] = sm[k] = 0.0f;
+                for (int pr = 0; pr < TB / 2; ++pr) HI[pr] = LO[pr] = SM[pr] = 0ull;
                 // X = A - B = -((-A) + B): both chains through one code copy
 #pragma unroll 1
                 for (int c = 0; c < 2; ++c) {
-                    tdi_chain<T>(P, sh, ny, smf, Lblk, dLf, ch, c, b, kmax, hi, lo, sm);
+                    tdi_chain<T>(P, sh, ny, smf, Lblk, dLf, ch, c, b, kmax, HI, LO, SM);
 #pragma unroll
-                    for (int k = 0; k < TB; ++k) {
-                        hi[k] = -hi[k];
-                        lo[k] = -lo[k];
-                        sm[k] = -sm[k];
+                    for (int pr = 0; pr < TB / 2; ++pr) {
+                        HI[pr] = fneg2(HI[pr]);
+                        LO[pr] = fneg2(LO[pr]);
+                        SM[pr] = fneg2(SM[pr]);
                     }
                 }
                 double *o = ts.ti.out + ch * ts.ti.N + ts.ti.n0 + i0;
 #pragma unroll
                 for (int k = 0; k < TB; ++k)
-                    if (k < kmax) o[k] = ff2d_scaled(hi[k], lo[k] + sm[k], sh.unscale_e);
+                    if (k < kmax)
+                        o[k] = ff2d_scaled(lane(HI[k >> 1], k & 1), lane(LO[k >> 1], k & 1) + lane(SM[k >> 1], k & 1),
+                                           sh.unscale_e);
             }
         }
         __syncthreads();
