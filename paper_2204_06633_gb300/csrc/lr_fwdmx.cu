@@ -644,6 +644,44 @@ __device__ __forceinline__ ff strain_anchor(const float *smf, int pol, int ai, f
     return {t2.hi, lo};
 }
 
+// strain_anchor on a pair of samples at once (packed lanes; per lane the same arithmetic as the
+// scalar form with the signs of intermediate error terms carried negated, which rounds
+// identically): EH, EL, NEH = -EH of the two samples, C their correction sums; returns the
+// unnormalised float-float pairs (HI, LO)
+template <int T>
+__device__ __forceinline__ void strain_anchor2(const float *smf, int pol, int a0, int a1, unsigned long long EH,
+                                               unsigned long long NEH, unsigned long long EL, unsigned long long C,
+                                               unsigned long long &HI, unsigned long long &LO)
+{
+    auto ld = [&](int arr) { return f2pack(smf[warr(pol, arr) + a0], smf[warr(pol, arr) + a1]); };
+    const unsigned long long SHI = ld(A_SHI), SLO = ld(A_SLO), DHI = ld(A_DHI), DLO = ld(A_DLO);
+    const unsigned long long Pp = fmul2(EH, DHI);
+    const unsigned long long NPE = ffma2(NEH, DHI, Pp);  // -(eh dhi - p)
+    unsigned long long S1, E1;
+    two_sum2(SHI, Pp, S1, E1);
+    const unsigned long long LIN = fsub2(ffma2(EH, DLO, fmul2(EL, DHI)), NPE);
+    if constexpr (T < 4) {
+        HI = S1;
+        LO = fadd2(fadd2(SLO, E1), LIN);
+    } else {
+        const unsigned long long AHI = ld(A_A), ALO = ld(A_ALO);
+        const unsigned long long ONE = f2pack(1.0f, 1.0f);
+        const unsigned long long EM1 = fsub2(EH, ONE);
+        const unsigned long long Q = fmul2(EH, EM1);
+        const unsigned long long NQ = fmul2(NEH, EM1);                                 // -q exactly
+        const unsigned long long NQE0 = ffma2(NEH, EM1, Q);                            // -(eh em1 - q)
+        const unsigned long long G = ffma2(f2pack(2.0f, 2.0f), EH, fneg2(ONE));        // 2 eh - 1
+        const unsigned long long QE = ffma2(EL, G, fneg2(NQE0));
+        const unsigned long long CQ = fmul2(Q, AHI);
+        const unsigned long long NCQE = ffma2(NQ, AHI, CQ);                            // -(q ahi - cq)
+        unsigned long long S2, E2;
+        two_sum2(S1, CQ, S2, E2);
+        HI = S2;
+        const unsigned long long CUR = fsub2(ffma2(Q, ALO, fmul2(QE, AHI)), NCQE);
+        LO = fsub2(fadd2(fadd2(fadd2(SLO, fadd2(E1, E2)), LIN), CUR), C);
+    }
+}
+
 __device__ __forceinline__ void store_read(float *smf, int rd, int pol, int j, ff v)
 {
     const int row = rd * 4 + pol * 2;
@@ -779,9 +817,17 @@ __device__ __forceinline__ void proj_item(float *smf, const TileSetup &sh, int r
             for (int k = 0; k < PB; ++k) C[k] = 0.0f;
         }
 #pragma unroll
-        for (int k = 0; k < PB; ++k) {
-            const ff v = strain_anchor<T>(smf, pol, o[(h + k) & 7] + ((h + k) >> 3), eh[k], el[k], C[k]);
-            if (k < kmax) store_read(smf, rd, pol, j0 + k, v);
+        for (int pr = 0; pr < PB / 2; ++pr) {
+            const int k0 = 2 * pr, k1 = 2 * pr + 1;
+            unsigned long long HI, LO;
+            strain_anchor2<T>(smf, pol, o[(h + k0) & 7] + ((h + k0) >> 3), o[(h + k1) & 7] + ((h + k1) >> 3),
+                              f2pack(eh[k0], eh[k1]), f2pack(-eh[k0], -eh[k1]), f2pack(el[k0], el[k1]),
+                              f2pack(C[k0], C[k1]), HI, LO);
+            float h0, h1, l0, l1;
+            f2unpack(HI, h0, h1);
+            f2unpack(LO, l0, l1);
+            if (k0 < kmax) store_read(smf, rd, pol, j0 + k0, {h0, l0});
+            if (k1 < kmax) store_read(smf, rd, pol, j0 + k1, {h1, l1});
         }
     }
 }
