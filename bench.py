@@ -39,6 +39,10 @@ FLOPS_PER_SAMPLE = lambda p: 273 * (p + 1) + 500  # noqa: E731
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (nominal; our DFMA probe measured 1.20)
 # FP32 ALU peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) per output sample of the fused mixed kernel at order 25 and its
+# default tile, from one ncu capture of a 16-source batch (236.4 MB / 7 115 014 outputs); the
+# launch traffic is this times the launch's outputs.  Valid only for that kernel build.
+MIXED_P25_DRAM_BYTES_PER_SAMPLE = 236_356_096 / 7_115_014
 
 
 def workload(rank: int, n_sources: int):
@@ -317,6 +321,10 @@ def run_ours(args):
         if rank == 0 and not args.no_check:
             fp64["rel_error_vs_oracle"] = sampled_error(d_xyz, lens, srcs, out_off, orb, p)
 
+    split = None
+    if rank == 0 and not args.no_split:
+        split = split_times(lr, ctx, p, dev, stream)
+
     if rank != 0:
         return
     avg_launch_s = statistics.mean(launch_ms) * 1e-3
@@ -326,8 +334,11 @@ def run_ours(args):
     else:
         peak_tflops, src_peak = FP32_PEAK_TFLOPS, ("FP32 ALU peak 152 SM x 128 lanes x 2 flop x 2.07 GHz "
                                                    "(own FFMA probe: 74.9 TFLOP/s)")
+    traffic = None
+    if precision == lr.MIXED and p == 25 and not args.tile:
+        traffic = MIXED_P25_DRAM_BYTES_PER_SAMPLE * total_samples
     roof = {"bound": "alu", "achieved": flops / avg_launch_s / 1e12, "peak": peak_tflops, "unit": "TFLOP/s",
-            "frac": flops / avg_launch_s / 1e12 / peak_tflops, "traffic": None, "peak_source": src_peak,
+            "frac": flops / avg_launch_s / 1e12 / peak_tflops, "traffic": traffic, "peak_source": src_peak,
             "algorithmic_flops_per_sample": FLOPS_PER_SAMPLE(p),
             "kernel": "k_mixed<T,FUSED>" if precision == lr.MIXED else "k_fused64<T>",
             "timing": "CUDA events around each batched call on its stream (tile-table kernel + fused kernel; "
@@ -343,10 +354,50 @@ def run_ours(args):
                        "samples_per_gpu": total_samples, "l2": "inputs (%.1f GB) larger than L2" %
                        ((hp.nbytes + hc.nbytes) / 1e9), "tile": plan.desc.tile},
             "rel_error_vs_oracle": rel_err, "roofline": roof, "e2e": e2e, "gpu_launches": (3 if precision == lr.MIXED else 2) * args.steps,
-            "clocks": clocks, "fp64": fp64}
+            "clocks": clocks, "fp64": fp64, "split": split}
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = oracle_rate(lens, srcs, p, orb)
     print(json.dumps(line), flush=True)
+
+
+def split_times(lr, ctx, p, dev, stream, reps=5):
+    """The paper's split on its own workload: one one-year source (N = 3,153,600 at dt = 10 s),
+    projection alone (h -> six links), TDI-2 alone (links -> X, Y, Z) and the fused call, in each
+    precision; CUDA events on the launching stream, median of `reps` after 3 warm-up calls."""
+    import torch
+
+    N = 3_153_600
+    orb = synth.orbit_flexing(T0 - 3e5, T0 + DT * N + 3e5)
+    o = lr.Orbit(ctx, orb.t_knots, orb.pos, None)
+    src = synth.draw_sources(1, seed=1, A=1e-21, fdot=1e-17)[0]
+    t0h, hp, hc = synth.gb_input(src, T0, DT, N, p)
+    d_hp = torch.tensor(hp, device=dev)
+    d_hc = torch.tensor(hc, device=dev)
+    sky = (src.lam, src.beta, src.psi)
+    y = torch.empty(6 * N, dtype=torch.float64, device=dev)
+    xyz = torch.empty(3 * N, dtype=torch.float64, device=dev)
+    out = {"workload": "one source, N = 3,153,600 (one year at dt 10 s), flexing orbit, order %d" % p}
+    for name, prec in (("mixed", lr.MIXED), ("fp64", lr.FP64)):
+        plan = lr.Plan(ctx, p, N, DT, o, t0=T0, precision=prec)
+        calls = {"project": lambda: plan.project(d_hp, d_hc, t0h, sky, y, stream=stream),
+                 "tdi": lambda: plan.tdi(y, xyz, stream=stream),
+                 "fused": lambda: plan.response(d_hp, d_hc, t0h, sky, xyz, stream=stream)}
+        res = {}
+        for k, f in calls.items():
+            for _ in range(3):
+                f()
+            ts = []
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                f()
+                b.record(stream)
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            res[k + "_ms"] = statistics.median(ts)
+        plan.check(stream)
+        out[name] = res
+    return out
 
 
 def sampled_error(d_xyz, lens, srcs, out_off, orb, p, n_sources=6, n_idx=60):
@@ -374,6 +425,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison run")
+    ap.add_argument("--no-split", action="store_true",
+                    help="skip the projection / TDI / fused split on one one-year source")
     ap.add_argument("--order", type=int, default=ORDER)
     ap.add_argument("--sources", type=int, default=S_SOURCES)
     ap.add_argument("--tile", type=int, default=0)
