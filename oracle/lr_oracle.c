@@ -26,7 +26,8 @@
  * Readings where the paper is silent (order = polynomial degree p, odd; stencil
  * m-(p-1)/2 .. m+(p+1)/2 around m = floor(x); zero extension outside the supplied
  * samples; integer sample index kept exact in read positions; Newtonian light-time solve
- * when delays are not given; nested delays as an option) are listed in the design doc.
+ * when delays are not given; nested delays as an option) are the documented readings of the
+ * library.
  *
  * Parity status: every function here is pinned by tests/test_oracle_*.py (closed forms,
  * invariants, library routines, brute force), except the whole pipeline on generic
