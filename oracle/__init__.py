@@ -75,6 +75,8 @@ def _load():
             "orc_project_adjoint": (I, [I, D, D, I64, P, I64, D, D, D, D, dp, dp, dp]),
             "orc_sky_gradient": (I, [I, D, D, I64, P, dp, dp, I64, D, D, D, D, dp, dp]),
             "orc_sky_gradient_abs": (I, [I, D, D, I64, P, dp, dp, I64, D, D, D, D, dp, dp]),
+            "orc_aet": (None, [dp, I64, dp]),
+            "orc_like_inner": (None, [dp, dp, I64, dp, dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -255,3 +257,25 @@ def backward(p, gen, dt, t0, n, porb, torb, hp, hc, t0h, lam, beta, psi, gxyz, d
     if with_scale:
         return ghp, ghc, gsky, sky_gradient(p, dt, t0, n, porb, hp, hc, t0h, lam, beta, psi, gy, absval=True)
     return ghp, ghc, gsky
+
+
+# ---------------------------------------------------------------- likelihood
+def aet(xyz) -> np.ndarray:
+    """A, E, T of X, Y, Z ([3][n] -> [3][n]); Sec. "Time-delay interferometry"."""
+    x = _f64(xyz).reshape(3, -1)
+    out = np.empty_like(x)
+    _load().orc_aet(_dp(x), x.shape[1], _dp(out))
+    return out
+
+
+def like_inner(xyz, data_aet, w=(1.0, 1.0, 1.0)):
+    """(<d|h>, <h|h>) of the template with X, Y, Z `xyz` against data given in A, E, T, white
+    noise of variance 1/w_c per channel (Eq. like, time domain)."""
+    x = _f64(xyz).reshape(3, -1)
+    d = _f64(data_aet).reshape(3, -1)
+    if d.shape != x.shape:
+        raise ValueError("data and template lengths differ")
+    ww = _f64(w).reshape(3)
+    out = np.empty(2)
+    _load().orc_like_inner(_dp(x), _dp(d), x.shape[1], _dp(ww), _dp(out))
+    return float(out[0]), float(out[1])

@@ -23,6 +23,10 @@
  *   - centered Lagrange interpolation ......... Sec. "Implementation"
  *   - orbit interpolation ..................... Sec. "Implementation" (orbits interpolated
  *                                            to the sample grid): cubic spline
+ *   - A, E, T channels ....................... Sec. "Time-delay interferometry" (the
+ *                                            uncorrelated combinations of X, Y, Z)
+ *   - likelihood inner products .............. Eq. (like), summed over A, E, T, in the time
+ *                                            domain with white noise per channel
  * Readings where the paper is silent (order = polynomial degree p, odd; stencil
  * m-(p-1)/2 .. m+(p+1)/2 around m = floor(x); zero extension outside the supplied
  * samples; integer sample index kept exact in read positions; Newtonian light-time solve
@@ -842,4 +846,37 @@ int orc_sky_gradient_abs(int p, double dt, double t0, int64_t N, const void *por
     }
     gsky[0] = G[0]; gsky[1] = G[1]; gsky[2] = G[2];
     return 0;
+}
+
+/* ------------------------------------------------------------------ likelihood
+ * Uncorrelated TDI channels (Sec. "Time-delay interferometry", the A, E, T combinations of
+ * X, Y, Z): A = (Z - X)/sqrt(2), E = (X - 2Y + Z)/sqrt(6), T = (X + Y + Z)/sqrt(3).
+ * xyz and aet are [3][n] (channel-major). */
+void orc_aet(const double *xyz, int64_t n, double *aet)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        const double X = xyz[i], Y = xyz[n + i], Z = xyz[2 * n + i];
+        aet[i] = (Z - X) / sqrt(2.0);
+        aet[n + i] = (X - 2.0 * Y + Z) / sqrt(6.0);
+        aet[2 * n + i] = (X + Y + Z) / sqrt(3.0);
+    }
+}
+
+/* Inner products of the log-likelihood (Eq. like: log L = -(<d|d> + <h|h> - 2 <d|h>)/2), summed
+ * over the channels A, E, T as the paper does, in the time domain with white noise of variance
+ * 1/w_c in channel c: <a|b> = sum_c w_c sum_i a_c[i] b_c[i].  The template is given by its
+ * X, Y, Z (xyz, [3][n]); the data by its A, E, T (data, [3][n]).  out = {<d|h>, <h|h>}. */
+void orc_like_inner(const double *xyz, const double *data, int64_t n, const double *w, double *out)
+{
+    double *h = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    orc_aet(xyz, n, h);
+    double dh = 0.0, hh = 0.0;
+    for (int c = 0; c < 3; ++c)
+        for (int64_t i = 0; i < n; ++i) {
+            dh += w[c] * data[c * n + i] * h[c * n + i];
+            hh += w[c] * h[c * n + i] * h[c * n + i];
+        }
+    free(h);
+    out[0] = dh;
+    out[1] = hh;
 }
