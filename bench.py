@@ -307,6 +307,33 @@ def run_ours(args):
                "d2h_bytes_per_step": int(out_pin.numel() * 8), "ms_per_step": t,
                "api": "lr_response_batched_host (host buffers; chunked copy-in, kernel and copy-out overlapped)"}
 
+    # fused likelihood epilogue on the same batch: A, E, T and the inner products per tile, X, Y, Z
+    # not written; the data is the batch's own response (values do not change the work)
+    like = None
+    if not args.no_like:
+        data = d_xyz.clone()
+        dhh = torch.empty((args.sources, 2), dtype=torch.float64, device=dev)
+
+        def like_step():
+            plan.likelihood_batched(d_hoff, d_ooff, d_t0h, d_sky, d_hp, d_hc, data, out=dhh, stream=stream)
+
+        for _ in range(args.warmup):
+            like_step()
+        torch.cuda.synchronize()
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            like_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        plan.check(stream)
+        ms_like = max_over_ranks(a.elapsed_time(b) / args.steps)
+        like = {"value": link_samples / (ms_like * 1e-3), "unit": "link-samples/s", "ms_per_step": ms_like,
+                "steps": args.steps, "warmup": args.warmup, "ms_response_per_step": ms_step,
+                "api": "lr_likelihood_batched (per source <d|h>, <h|h> over A, E, T; X, Y, Z not written)"}
+        del data
+
     # the same batch in plain FP64 on the same GPU (the comparison the metric names)
     fp64 = None
     if precision == lr.MIXED and not args.no_fp64:
@@ -354,7 +381,7 @@ def run_ours(args):
                        "samples_per_gpu": total_samples, "l2": "inputs (%.1f GB) larger than L2" %
                        ((hp.nbytes + hc.nbytes) / 1e9), "tile": plan.desc.tile},
             "rel_error_vs_oracle": rel_err, "roofline": roof, "e2e": e2e, "gpu_launches": (3 if precision == lr.MIXED else 2) * args.steps,
-            "clocks": clocks, "fp64": fp64, "split": split}
+            "clocks": clocks, "fp64": fp64, "split": split, "likelihood": like}
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = oracle_rate(lens, srcs, p, orb)
     print(json.dumps(line), flush=True)
@@ -425,6 +452,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison run")
+    ap.add_argument("--no-like", action="store_true", help="skip the fused likelihood timing")
     ap.add_argument("--no-split", action="store_true",
                     help="skip the projection / TDI / fused split on one one-year source")
     ap.add_argument("--order", type=int, default=ORDER)

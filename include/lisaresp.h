@@ -224,6 +224,34 @@ LR_API int lr_response_batched_noalloc(lr_plan *plan, int64_t S, const int64_t *
                                        const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
                                        double *xyz, void *stream);
 
+/* ------------------------------------------------------------------ likelihood */
+/* Fused likelihood epilogue of the forward (the log-likelihood of Eq. like,
+ * log L = -(<d|d> + <h|h> - 2 <d|h>)/2, with the inner product summed over the uncorrelated
+ * channels A = (Z - X)/sqrt 2, E = (X - 2Y + Z)/sqrt 6, T = (X + Y + Z)/sqrt 3 of Sec.
+ * "Time-delay interferometry").  The inner product is taken in the time domain with white noise
+ * of variance 1/w_c in channel c: <a|b> = sum_c w_c sum_n a_c[n] b_c[n] (the paper weights it
+ * by a noise PSD in the frequency domain; that needs the whole series and is not fused here).
+ * Each tile of the fused forward forms A, E, T of its outputs on chip and its partial sums; a
+ * second kernel adds the tiles of each source in a fixed order (deterministic, no atomics).
+ *   data    : DEVICE [3][plan.n], the data in A, E, T (channel-major)
+ *   weights : HOST double[3], w_A, w_E, w_T (finite, >= 0)
+ *   dh_hh   : DEVICE double[2], written with <d|h>, <h|h> (<d|d> is the caller's constant)
+ *   xyz     : DEVICE [3][plan.n] receiving X, Y, Z as lr_response, or NULL (not written)
+ * Allocates the plan's per-tile partial buffer on first use (freed with the plan).
+ * Errors as lr_response; LR_ERR_INVALID_ARG for a negative or non-finite weight. */
+LR_API int lr_likelihood(lr_plan *plan, const double *hp, const double *hc, int64_t n_h, double t0_h,
+                         lr_sky sky, const double *data, const double *weights, double *dh_hh, double *xyz,
+                         void *stream);
+/* Batched form: offsets, times and sky as lr_response_batched; data is DEVICE packed like xyz
+ * (source s at data[3*out_off[s] ..] as [3][n_s]) and holds n_total = out_off[S] samples per
+ * channel block; dh_hh is DEVICE [S][2].  Sources whose offsets run past n_total get NaN and
+ * record LR_ERR_DEVICE (read with lr_plan_check); no read goes past the data.  S <= 2^24,
+ * n_total <= 2^40. */
+LR_API int lr_likelihood_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
+                                 const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
+                                 const double *data, int64_t n_total, const double *weights, double *dh_hh,
+                                 double *xyz, void *stream);
+
 /* Batched transpose; g_sky is DEVICE [S][3] (may be NULL). */
 LR_API int lr_backward_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
                                const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,

@@ -72,6 +72,8 @@ _SIGS = {
     "lr_graph_launch": (_I, [_P, _P]),
     "lr_graph_destroy": (_I, [_P]),
     "lr_plan_autotune": (_I, [_P, _I64, _I, _P, ctypes.POINTER(_I)]),
+    "lr_likelihood": (_I, [_P, _P, _P, _I64, _D, lr_sky, _P, _P, _P, _P, _P]),
+    "lr_likelihood_batched": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _P, _P, _P]),
 }
 NOALLOC_MAX_SOURCES = 65536
 
@@ -281,6 +283,35 @@ class Plan:
             _dev64(sky, "sky", 3 * S), _dev64(hp, "hp"), _dev64(hc, "hc", hp.numel()), _dev64(xyz, "xyz"),
             _stream_handle(stream)))
         return xyz
+
+    def likelihood(self, hp, hc, t0h, sky, data, weights=(1.0, 1.0, 1.0), xyz=None, out=None, stream=None):
+        """(<d|h>, <h|h>) as a float64 CUDA tensor [2]: the template's A, E, T against `data`
+        (float64 CUDA [3][n] in A, E, T), white noise of variance 1/w_c per channel; the fused
+        forward forms them tile by tile.  xyz (optional) also receives X, Y, Z."""
+        out = self._out(out, (2,), hp)
+        w = (ctypes.c_double * 3)(*[float(x) for x in weights])
+        _check("lr_likelihood", library().lr_likelihood(
+            self._h, _dev64(hp, "hp"), _dev64(hc, "hc", hp.numel()), hp.numel(), float(t0h), _sky(sky),
+            _dev64(data, "data", 3 * self.n), ctypes.addressof(w), _dev64(out, "dh_hh", 2),
+            _dev64(xyz, "xyz", 3 * self.n) if xyz is not None else None, _stream_handle(stream)))
+        return out
+
+    def likelihood_batched(self, h_off, out_off, t0h, sky, hp, hc, data, weights=(1.0, 1.0, 1.0), xyz=None,
+                           out=None, stream=None):
+        """Per-source (<d|h>, <h|h>) as float64 CUDA [S][2]; data packed like the batched xyz
+        (float64 CUDA [3 * sum N_s], source s at 3 out_off[s] as [3][N_s], in A, E, T)."""
+        S = t0h.numel()
+        if data.numel() % 3:
+            raise ValueError("data must hold three channel blocks")
+        n_total = data.numel() // 3
+        out = self._out(out, (S, 2), hp)
+        w = (ctypes.c_double * 3)(*[float(x) for x in weights])
+        _check("lr_likelihood_batched", library().lr_likelihood_batched(
+            self._h, S, _devi64(h_off, "h_off", S + 1), _devi64(out_off, "out_off", S + 1), _dev64(t0h, "t0h", S),
+            _dev64(sky, "sky", 3 * S), _dev64(hp, "hp"), _dev64(hc, "hc", hp.numel()),
+            _dev64(data, "data", 3 * n_total), n_total, ctypes.addressof(w), _dev64(out, "dh_hh", 2 * S),
+            _dev64(xyz, "xyz", 3 * n_total) if xyz is not None else None, _stream_handle(stream)))
+        return out
 
     def response_batched_host(self, h_off, out_off, t0h, sky, hp, hc, xyz=None, stream=None):
         """The batched response on host arrays (numpy or CPU tensors; page-locked tensors let

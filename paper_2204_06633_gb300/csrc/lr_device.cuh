@@ -68,11 +68,24 @@ struct TileInfo {
     const double *hp, *hc;
     double *out;      // base of this source's output block
     const double *yin;
+    const double *dat;  // base of this source's A, E, T data (likelihood launches), else null
     int ok;
 };
 
 // Maps global tile g to its source.  `ochan` is the number of output channels (3 for TDI,
 // 6 for link series).
+// A, E, T data block of the source with outputs [oo, oo1): null (and ERR_OFFSETS) when the
+// offsets run past the data the caller declared
+__device__ inline const double *like_data(const FwdParams &P, int64_t oo, int64_t oo1)
+{
+    if (!P.like.data) return nullptr;
+    if (oo < 0 || oo1 < oo || oo1 > P.like.n_total) {
+        atomicOr(P.err, ERR_OFFSETS);
+        return nullptr;
+    }
+    return P.like.data + 3 * oo;
+}
+
 __device__ inline TileInfo tile_info(const FwdParams &P, int64_t g, int ochan)
 {
     TileInfo ti;
@@ -86,6 +99,7 @@ __device__ inline TileInfo tile_info(const FwdParams &P, int64_t g, int ochan)
         ti.hc = P.hc;
         ti.out = P.out;
         ti.yin = P.yin;
+        ti.dat = P.like.data;
         ti.n0 = g * P.tile;
     } else {
         const int64_t *to = P.src.tile_off;
@@ -104,8 +118,9 @@ __device__ inline TileInfo tile_info(const FwdParams &P, int64_t g, int ochan)
         ti.sky = P.src.sky[s];
         ti.hp = P.hp + ho;
         ti.hc = P.hc + ho;
-        ti.out = P.out + ochan * oo;
+        ti.out = P.out ? P.out + ochan * oo : nullptr;
         ti.yin = P.yin ? P.yin + 6 * oo : nullptr;
+        ti.dat = like_data(P, oo, oo1);
         ti.n0 = (g - __ldg(to + s)) * P.tile;
     }
     int64_t rem = ti.N - ti.n0;
@@ -188,6 +203,59 @@ __device__ __forceinline__ void read2(const double *a, const double *b, int64_t 
         return;
     }
     horner2<T>(a + st, b + st, e, ra, rb);
+}
+
+
+// ---------------------------------------------------------------- likelihood epilogue
+// Adds the terms of output sample n (X, Y, Z of the template) to the partial inner products
+// <d|h> and <h|h> over the channels A = (Z - X)/sqrt 2, E = (X - 2 Y + Z)/sqrt 6,
+// T = (X + Y + Z)/sqrt 3 with weights w; dat is the source's data block [3][N] in A, E, T.
+__device__ inline void like_terms(const LikeArgs &L, const double *dat, int64_t N, int64_t n, double X, double Y,
+                                  double Z, double &dh, double &hh)
+{
+    const double R2 = 0.70710678118654752440, R6 = 0.40824829046386301637, R3 = 0.57735026918962576451;
+    const double a = (Z - X) * R2, e = (X - 2.0 * Y + Z) * R6, t = (X + Y + Z) * R3;
+    const double wa = L.w[0] * a, we = L.w[1] * e, wt = L.w[2] * t;
+    dh = fma(wa, __ldg(dat + n), fma(we, __ldg(dat + N + n), fma(wt, __ldg(dat + 2 * N + n), dh)));
+    hh = fma(wa, a, fma(we, e, fma(wt, t, hh)));
+}
+
+// Block sum of (a, b) in a fixed order (shuffle tree within warps, then warps in index order);
+// red holds 2 doubles per warp.  Every thread of the block must call it; thread 0 gets the sums.
+__device__ inline void block_sum2(double &a, double &b, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[2 * w] = a;
+        red[2 * w + 1] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa = 0.0, sb = 0.0;
+        for (int i = 0; i < nw; ++i) {
+            sa += red[2 * i];
+            sb += red[2 * i + 1];
+        }
+        a = sa;
+        b = sb;
+    }
+}
+
+__device__ inline double nan_d() { return __longlong_as_double(0x7ff8000000000000ll); }
+
+// tile g's partial, or ERR_OFFSETS when g is past the partial buffer
+__device__ inline void like_store(const FwdParams &P, int64_t g, double dh, double hh)
+{
+    if (g < 0 || g >= P.like.cap) {
+        atomicOr(P.err, ERR_OFFSETS);
+        return;
+    }
+    P.like.partial[2 * g] = dh;
+    P.like.partial[2 * g + 1] = hh;
 }
 
 }  // namespace lr

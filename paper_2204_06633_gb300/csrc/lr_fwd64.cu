@@ -115,12 +115,15 @@ __global__ void __launch_bounds__(256) k_fused64(FwdParams P)
     double *hwp = sm, *hwc = sm + P.wmax, *ys = sm + 2 * P.wmax;
     __shared__ TileInfo ti;
     __shared__ SkyConst skc;
+    __shared__ double red[2 * 32];
+    const bool like = P.like.data != nullptr;
     const int64_t total = P.total_tiles >= 0 ? P.total_tiles : P.src.tile_off[P.src.S];
     for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
         if (threadIdx.x == 0) {
             ti = tile_info(P, g, 3);
             skc = make_sky(ti.sky);
             if (!ti.ok) atomicOr(P.err, ERR_OFFSETS);
+            if (like && !(ti.ok && ti.nb > 0)) like_store(P, g, 0.0, 0.0);
         }
         __syncthreads();
         if (ti.ok && ti.nb > 0) {
@@ -146,12 +149,20 @@ __global__ void __launch_bounds__(256) k_fused64(FwdParams P)
                 for (int l = 0; l < 6; ++l) ys[l * P.ymax + j] = y[l];
             }
             __syncthreads();
+            double dh = 0.0, hh = 0.0;  // likelihood partials of this thread's outputs
             for (int i = threadIdx.x; i < ti.nb; i += blockDim.x) {
                 int64_t n = ti.n0 + i;
                 double o[3];
                 tdi_sample64<T>(P, n, ys, P.ymax, k_lo, ny, o);
+                if (ti.out) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) ti.out[c * ti.N + n] = o[c];
+                    for (int c = 0; c < 3; ++c) ti.out[c * ti.N + n] = o[c];
+                }
+                if (like && ti.dat) like_terms(P.like, ti.dat, ti.N, n, o[0], o[1], o[2], dh, hh);
+            }
+            if (like) {
+                block_sum2(dh, hh, red);
+                if (threadIdx.x == 0) like_store(P, g, ti.dat ? dh : nan_d(), ti.dat ? hh : nan_d());
             }
         }
         __syncthreads();

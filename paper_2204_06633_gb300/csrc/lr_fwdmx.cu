@@ -53,6 +53,11 @@ static_assert(OFF_TW % 4 == 0, "weights must be 16-byte aligned");
 static_assert(2 * MX_WCAP * 2 <= 36 * MX_AY, "FP64 strain staging fits the link region");
 static_assert(6 * MX_YCAP * 2 <= 14 * MX_AW, "FP64 link staging fits the strain region");
 static_assert(6 * LB * 2 + 6 * LT <= 14 * MX_AW, "the delay tables fit the strain region");
+// X, Y, Z of a tile for the likelihood epilogue (FP64, after the delay tables)
+constexpr int XYZ_CAP = MX_TDI_BLOCK * (MIXED_THREADS / 3);  // largest mixed tile
+constexpr int OFF_XYZ = OFF_W + 6 * LB * 2 + 6 * LT;
+static_assert(OFF_XYZ % 2 == 0 && OFF_XYZ + 2 * 3 * XYZ_CAP <= OFF_W + 14 * MX_AW,
+              "the likelihood staging fits the strain region after the delay tables");
 
 // packed pairs of FP32 values and their fused multiply-add (fma.rn.f32x2: two IEEE FMAs in one
 // instruction)
@@ -152,6 +157,7 @@ struct MxShared {
     // TDI reference per delayed term (current tile)
     int tfm[NTERM];
     float tehi[NTERM];
+    double red[2 * (MIXED_THREADS / 32)];  // likelihood block sums
 };
 
 // setup lanes: read-position and link-delay pieces on the first 30 lanes of warp 6, geometry
@@ -232,6 +238,7 @@ __device__ inline void mx_tile(const FwdParams &P, int64_t g, int ochan, int64_t
         ti.hc = P.hc;
         ti.out = P.out;
         ti.yin = P.yin;
+        ti.dat = P.like.data;
         ti.n0 = g * P.tile;
         sk = P.src.skyc1;
     } else {
@@ -261,8 +268,9 @@ __device__ inline void mx_tile(const FwdParams &P, int64_t g, int ochan, int64_t
         ti.sky = P.src.sky[s];
         ti.hp = P.hp + ho;
         ti.hc = P.hc + ho;
-        ti.out = P.out + ochan * oo;
+        ti.out = P.out ? P.out + ochan * oo : nullptr;
         ti.yin = P.yin ? P.yin + 6 * oo : nullptr;
+        ti.dat = like_data(P, oo, oo1);
         ti.n0 = (g - __ldg(to + s)) * P.tile;
         sk = P.src.skyc[s];
     }
@@ -1082,6 +1090,7 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
             __syncthreads();
         }
         if (!ts.ti.ok || ts.ti.nb <= 0) {
+            if (KIND == KIND_FUSED && P.like.data && tid == 0) like_store(P, g, 0.0, 0.0);
             if (next) {
                 if (tid == 0) tile_begin<KIND>(P, sh, tn, gn);
                 __syncthreads();
@@ -1239,12 +1248,30 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
                         SM[pr] = fneg2(SM[pr]);
                     }
                 }
-                double *o = ts.ti.out + ch * ts.ti.N + ts.ti.n0 + i0;
+                double *o = ts.ti.out ? ts.ti.out + ch * ts.ti.N + ts.ti.n0 + i0 : nullptr;
+                double *xs = KIND == KIND_FUSED && P.like.data
+                                 ? reinterpret_cast<double *>(smf + OFF_XYZ) + ch * XYZ_CAP + i0
+                                 : nullptr;
 #pragma unroll
                 for (int k = 0; k < TB; ++k)
-                    if (k < kmax)
-                        o[k] = ff2d_scaled(lane(HI[k >> 1], k & 1), lane(LO[k >> 1], k & 1) + lane(SM[k >> 1], k & 1),
-                                           sh.unscale_e);
+                    if (k < kmax) {
+                        const double v = ff2d_scaled(lane(HI[k >> 1], k & 1),
+                                                     lane(LO[k >> 1], k & 1) + lane(SM[k >> 1], k & 1), sh.unscale_e);
+                        if (o) o[k] = v;
+                        if (xs) xs[k] = v;
+                    }
+            }
+            // ---- likelihood epilogue: A, E, T of the tile against the data, block sums
+            if (KIND == KIND_FUSED && P.like.data) {
+                __syncthreads();
+                const double *xs = reinterpret_cast<const double *>(smf + OFF_XYZ);
+                double dh = 0.0, hh = 0.0;
+                if (ts.ti.dat)
+                    for (int i = tid; i < nb; i += blockDim.x)
+                        like_terms(P.like, ts.ti.dat, ts.ti.N, ts.ti.n0 + i, xs[i], xs[XYZ_CAP + i],
+                                   xs[2 * XYZ_CAP + i], dh, hh);
+                block_sum2(dh, hh, sh.red);
+                if (tid == 0) like_store(P, g, ts.ti.dat ? dh : nan_d(), ts.ti.dat ? hh : nan_d());
             }
         }
         __syncthreads();

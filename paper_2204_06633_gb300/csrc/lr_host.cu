@@ -52,6 +52,9 @@ struct lr_plan {
     int64_t ktile_cap;
     // host-buffer pipeline (lr_response_batched_host), created on first use
     lr::PipeWork *pipe;
+    // per-tile likelihood partials
+    double *d_lpart;
+    int64_t lpart_cap;
 };
 
 namespace lr {
@@ -436,6 +439,8 @@ LR_API int lr_plan_create(lr_ctx *ctx, const lr_plan_desc *d, lr_plan **out)
     p->d_ktile_off = p->d_htile_off = nullptr;
     p->ktile_cap = 0;
     p->pipe = nullptr;
+    p->d_lpart = nullptr;
+    p->lpart_cap = 0;
     lr::FwdParams &P = p->base;
     std::memset(&P, 0, sizeof(P));
     P.dt = d->dt;
@@ -510,6 +515,7 @@ LR_API int lr_plan_destroy(lr_plan *plan)
     if (plan->d_partial) cudaFree(plan->d_partial);
     if (plan->d_ktile_off) cudaFree(plan->d_ktile_off);
     if (plan->d_htile_off) cudaFree(plan->d_htile_off);
+    if (plan->d_lpart) cudaFree(plan->d_lpart);
     lr::pipe_free(plan->pipe);
     delete plan;
     return LR_OK;
@@ -686,6 +692,98 @@ LR_API int lr_response_batched(lr_plan *plan, int64_t S, const int64_t *h_off, c
     P.total_tiles = -1;
     return check_launch(plan->ctx, lr::launch_forward(plan->desc.precision, lr::KIND_FUSED, plan->desc.order, P,
                                                       plan->threads, plan->ctx->sms, stream));
+}
+
+}  // extern "C"
+
+namespace {
+
+// validates the weights and sizes the per-tile partial buffer for `tiles` tiles
+int like_setup(lr_plan *plan, const double *weights, int64_t tiles, lr::FwdParams &P, const double *data,
+               int64_t n_total)
+{
+    for (int c = 0; c < 3; ++c)
+        if (!std::isfinite(weights[c]) || weights[c] < 0.0) return LR_ERR_INVALID_ARG;
+    if (tiles > plan->lpart_cap) {
+        if (plan->d_lpart) cudaFree(plan->d_lpart);
+        plan->d_lpart = nullptr;
+        plan->lpart_cap = 0;
+        cudaError_t e = lr::dev_malloc((void **)&plan->d_lpart, sizeof(double) * 2 * (size_t)tiles);
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LR_ERR_OOM : cuda_fail(plan->ctx, e);
+        plan->lpart_cap = tiles;
+    }
+    P.like.data = data;
+    for (int c = 0; c < 3; ++c) P.like.w[c] = weights[c];
+    P.like.partial = plan->d_lpart;
+    P.like.cap = plan->lpart_cap;
+    P.like.n_total = n_total;
+    return LR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+LR_API int lr_likelihood(lr_plan *plan, const double *hp, const double *hc, int64_t n_h, double t0_h, lr_sky sky,
+                         const double *data, const double *weights, double *dh_hh, double *xyz, void *stream)
+{
+    if (!plan || !hp || !hc || !data || !weights || !dh_hh) return LR_ERR_INVALID_ARG;
+    if (n_h < 1) return LR_ERR_INVALID_ARG;
+    if (!std::isfinite(t0_h) || !std::isfinite(sky.lam) || !std::isfinite(sky.beta) || !std::isfinite(sky.psi))
+        return LR_ERR_NONFINITE;
+    if (std::fabs(plan->desc.t0 - t0_h) / plan->desc.dt > 1e12) return LR_ERR_RANGE;
+    lr::FwdParams P = plan->base;
+    const int64_t n = plan->desc.n, tiles = (n + P.tile - 1) / P.tile;
+    int st = like_setup(plan, weights, tiles, P, data, n);
+    if (st) return st;
+    P.src.n1 = n;
+    P.src.nh1 = n_h;
+    P.src.t0h1 = t0_h;
+    P.src.sky1 = sky;
+    P.src.skyc1 = lr::make_sky(sky);
+    P.hp = hp;
+    P.hc = hc;
+    P.out = xyz;
+    st = launch_single(plan, lr::KIND_FUSED, P, stream);
+    if (st) return st;
+    return check_launch(plan->ctx, lr::launch_like_reduce(plan->d_lpart, nullptr, tiles, 1, plan->lpart_cap, dh_hh,
+                                                          plan->d_err, stream));
+}
+
+LR_API int lr_likelihood_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
+                                 const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
+                                 const double *data, int64_t n_total, const double *weights, double *dh_hh,
+                                 double *xyz, void *stream)
+{
+    if (!plan || !h_off || !out_off || !t0_h || !sky || !hp || !hc || !data || !weights || !dh_hh)
+        return LR_ERR_INVALID_ARG;
+    if (S < 1 || n_total < 0) return LR_ERR_INVALID_ARG;
+    if (S > (int64_t)1 << 24 || n_total > (int64_t)1 << 40) return LR_ERR_RANGE;
+    int st = lr::plan_reserve_batch(plan, S);
+    if (st) return st;
+    lr::FwdParams P = plan->base;
+    // sum over sources of ceil(N_s / tile) <= n_total / tile + S
+    st = like_setup(plan, weights, n_total / P.tile + S, P, data, n_total);
+    if (st) return st;
+    lr::SkyConst *skyc = plan->desc.precision == LR_MIXED ? lr::plan_sky_table(plan) : nullptr;
+    int e = lr::launch_batch_tables(out_off, sky, S, P.tile, plan->d_tile_off, skyc, P.err, stream);
+    if (e) return check_launch(plan->ctx, e);
+    P.src.skyc = skyc;
+    P.src.h_off = h_off;
+    P.src.out_off = out_off;
+    P.src.t0h = t0_h;
+    P.src.sky = sky;
+    P.src.tile_off = plan->d_tile_off;
+    P.src.S = S;
+    P.hp = hp;
+    P.hc = hc;
+    P.out = xyz;
+    P.total_tiles = -1;
+    st = check_launch(plan->ctx, lr::launch_forward(plan->desc.precision, lr::KIND_FUSED, plan->desc.order, P,
+                                                    plan->threads, plan->ctx->sms, stream));
+    if (st) return st;
+    return check_launch(plan->ctx, lr::launch_like_reduce(plan->d_lpart, plan->d_tile_off, 0, S, plan->lpart_cap,
+                                                          dh_hh, plan->d_err, stream));
 }
 
 LR_API int lr_backward(lr_plan *plan, const double *hp, const double *hc, int64_t n_h, double t0_h, lr_sky sky,

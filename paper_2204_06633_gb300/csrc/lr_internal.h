@@ -77,6 +77,18 @@ struct SrcArgs {
     SkyConst skyc1;
 };
 
+// Fused likelihood epilogue of the forward launch (Eq. like in the time domain, summed over the
+// channels A, E, T of Sec. "Time-delay interferometry"): each tile leaves its partial
+// (<d|h>, <h|h>) in partial[2 g], [2 g + 1]; a second kernel sums the tiles of every source in
+// a fixed order.  data == nullptr: no likelihood.
+struct LikeArgs {
+    const double *data;  // data in A, E, T: [3][N_s] per source, at 3 out_off[s] (batched)
+    double w[3];         // channel weights (1 / noise variance of A, E, T)
+    double *partial;     // [cap][2]
+    int64_t cap;         // tiles the partial buffer holds
+    int64_t n_total;     // samples the data array holds per channel block (sum of N_s)
+};
+
 struct FwdParams {
     double dt, inv_dt, t0;
     OrbitDev po, to;      // projection orbit, TDI orbit
@@ -92,7 +104,8 @@ struct FwdParams {
     SrcArgs src;
     const double *hp, *hc;  // strain (h+, hx)
     const double *yin;      // link series input (TDI-only launches)
-    double *out;            // y [6][n] or xyz [3][n]
+    double *out;            // y [6][n] or xyz [3][n] (fused likelihood launches: may be null)
+    LikeArgs like;
     int *err;               // device error word
     int64_t total_tiles;    // >= 0 single source; -1: read src.tile_off[S]
     double cheb[4][4];      // monomial coefficients of the cubic through 4 Chebyshev nodes on [-1, 1]

@@ -91,4 +91,45 @@ int launch_batch_tables(const int64_t *out_off, const lr_sky *sky, int64_t S, in
     return (int)cudaGetLastError();
 }
 
+// Per-source sums of the likelihood partials: one warp per source adds its tiles' partials
+// (lane l takes tiles l, l + 32, ... in order, then a fixed shuffle tree), so the result does not
+// depend on the launch or on timing.  tile_off == nullptr: one source of tiles1 tiles.
+__global__ void __launch_bounds__(256) k_like_reduce(const double *__restrict__ partial,
+                                                     const int64_t *__restrict__ tile_off, int64_t tiles1,
+                                                     int64_t S, int64_t cap, double *__restrict__ out, int *err)
+{
+    const int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (s >= S) return;  // uniform over the warp
+    const int64_t a = tile_off ? tile_off[s] : 0, b = tile_off ? tile_off[s + 1] : tiles1;
+    if (a < 0 || b < a || b > cap) {
+        if (lane == 0) {
+            atomicOr(err, ERR_OFFSETS);
+            out[2 * s] = out[2 * s + 1] = __longlong_as_double(0x7ff8000000000000ll);
+        }
+        return;
+    }
+    double dh = 0.0, hh = 0.0;
+    for (int64_t g = a + lane; g < b; g += 32) {
+        dh += partial[2 * g];
+        hh += partial[2 * g + 1];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        dh += __shfl_down_sync(0xffffffffu, dh, o);
+        hh += __shfl_down_sync(0xffffffffu, hh, o);
+    }
+    if (lane == 0) {
+        out[2 * s] = dh;
+        out[2 * s + 1] = hh;
+    }
+}
+
+int launch_like_reduce(const double *partial, const int64_t *tile_off, int64_t tiles1, int64_t S, int64_t cap,
+                       double *out, int *err, void *stream)
+{
+    const int64_t blocks = (S + 7) / 8;
+    k_like_reduce<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(partial, tile_off, tiles1, S, cap, out, err);
+    return (int)cudaGetLastError();
+}
+
 }  // namespace lr

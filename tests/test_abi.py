@@ -54,3 +54,6 @@ def test_null_arguments_are_rejected_on_the_host(lib):
     assert lib.lr_plan_create(None, None, None) == 1
     assert lib.lr_orbit_destroy(None) == 1
     assert lib.lr_required_margin(None, None, None) == 1
+    assert lib.lr_likelihood(None, None, None, 0, 0.0, lr.lr_sky(), None, None, None, None, None) == 1
+    assert lib.lr_likelihood_batched(None, 1, None, None, None, None, None, None, None, 0, None, None, None,
+                                     None) == 1

@@ -1,0 +1,169 @@
+"""GPU parity of the fused likelihood epilogue (A, E, T of each tile against the data, per-tile
+partial inner products, per-source fixed-order sums) against the oracle.
+
+Two checks per case: (1) the epilogue alone, against the oracle's inner products of the X, Y, Z
+the same call returned (only the summation order differs: bound 1e-12 of the sum of |terms|);
+(2) end to end, against the oracle's inner products of the oracle's own response, with the bound
+the response's parity bound implies: |d<h|h>| <= (2 e + e^2) <h|h>, |d<d|h>| <= e sqrt(<d|d><h|h>)
+for a relative L2 response error e (channel weights within a factor wmax/wmin)."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_2204_06633_gb300 as lr  # noqa: E402
+import synth  # noqa: E402
+from _gpu import DT, T0, Pair, dev, host, parity_bound, sky  # noqa: E402
+
+SIGMA = 1e-21
+W = (1.0 / SIGMA**2, 2.0 / SIGMA**2, 0.5 / SIGMA**2)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return lr.Context(0)
+
+
+@pytest.fixture(scope="module")
+def flex(ctx):
+    return Pair(ctx, synth.orbit_flexing(-2e6, 3e5 * DT + 2e6))
+
+
+def epilogue_bound(xyz, data, w):
+    """Sum of |terms| of the two inner products, times 1e-12 (summation-order rounding)."""
+    a = np.abs(oracle.aet(xyz))
+    d = np.abs(data)
+    wa = np.asarray(w)[:, None]
+    return 1e-12 * float(np.sum(wa * a * d)), 1e-12 * float(np.sum(wa * a * a))
+
+
+def check_against_oracle(got, xyz_gpu, xyz_ref, scale, data, w, T, rel):
+    dh, hh = got
+    # (1) the epilogue, given the template the kernel formed
+    e_dh, e_hh = oracle.like_inner(xyz_gpu, data, w)
+    bdh, bhh = epilogue_bound(xyz_gpu, data, w)
+    assert abs(dh - e_dh) <= bdh, (dh, e_dh)
+    assert abs(hh - e_hh) <= bhh, (hh, e_hh)
+    # (2) end to end, from the response parity bound
+    r_dh, r_hh = oracle.like_inner(xyz_ref, data, w)
+    e = parity_bound(xyz_ref, scale, T, rel) / np.linalg.norm(xyz_ref)
+    wr = max(w) / min(w)
+    dd = float(np.sum(np.asarray(w)[:, None] * data * data))
+    assert abs(hh - r_hh) <= wr * (2 * e + e * e) * r_hh + bhh
+    assert abs(dh - r_dh) <= wr * e * math.sqrt(dd * r_hh) + bdh
+
+
+@pytest.mark.parametrize("precision,rel", [(lr.FP64, 1e-12), (lr.MIXED, 1e-6)])
+@pytest.mark.parametrize("N", [30001, 7])
+def test_single_source(ctx, flex, precision, rel, N):
+    p = 25
+    src = synth.draw_sources(1, seed=12, A=1e-21, fdot=1e-17)[0]
+    t0h, hp, hc = synth.gb_input(src, T0, DT, N, p)
+    args = (p, 2, DT, T0, N, flex.orc, flex.orc, hp, hc, t0h, src.lam, src.beta, src.psi)
+    ref = oracle.response(*args)
+    scale = oracle.response(*args, absval=True)
+    data = oracle.aet(ref + synth.white_noise(ref.shape, SIGMA, seed=5))
+    plan = lr.Plan(ctx, p, N, DT, flex.gpu, t0=T0, precision=precision)
+    xyz = torch.empty(3 * N, dtype=torch.float64, device="cuda:0")
+    d_hp, d_hc, d_data = dev(hp), dev(hc), dev(data)
+    got = host(plan.likelihood(d_hp, d_hc, t0h, sky(src), d_data, W, xyz=xyz))
+    plan.check()
+    check_against_oracle(got, host(xyz).reshape(3, N), ref, scale, data, W, p + 1, rel)
+    # without the X, Y, Z output: the same sums bit for bit, and the same X, Y, Z as lr_response
+    got2 = host(plan.likelihood(d_hp, d_hc, t0h, sky(src), d_data, W))
+    assert np.array_equal(got, got2)
+    assert np.array_equal(host(xyz), host(plan.response(d_hp, d_hc, t0h, sky(src))).ravel())
+    plan.check()
+
+
+def batch(lens, seed, p):
+    lens = np.asarray(lens, dtype=np.int64)
+    srcs = synth.draw_sources(len(lens), seed=seed, A=1e-21, fdot=1e-17)
+    m = synth.input_margin_samples(DT, p)
+    nh = lens + 2 * m
+    h_off = np.concatenate([[0], np.cumsum(nh)]).astype(np.int64)
+    out_off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    hp, hc = np.empty(h_off[-1]), np.empty(h_off[-1])
+    t0h = np.full(len(lens), T0 - m * DT)
+    for s, src in enumerate(srcs):
+        a, b = synth.gb_polarisations(src, synth.sample_grid(t0h[s], DT, int(nh[s])))
+        hp[h_off[s]:h_off[s + 1]], hc[h_off[s]:h_off[s + 1]] = a, b
+    sky_ = np.array([[x.lam, x.beta, x.psi] for x in srcs])
+    return srcs, h_off, out_off, t0h, sky_, hp, hc
+
+
+@pytest.mark.parametrize("precision,rel", [(lr.FP64, 1e-12), (lr.MIXED, 1e-6)])
+def test_batched_ragged_with_empty_and_tiny_sources(ctx, flex, precision, rel):
+    p = 11
+    lens = [9000, 0, 1, 2345, 341, 6000]
+    srcs, h_off, out_off, t0h, sky_, hp, hc = batch(lens, 31, p)
+    data = np.empty(3 * int(out_off[-1]))
+    refs = []
+    for s, src in enumerate(srcs):
+        N = lens[s]
+        if N == 0:
+            refs.append(None)
+            continue
+        args = (p, 2, DT, T0, N, flex.orc, flex.orc, hp[h_off[s]:h_off[s + 1]], hc[h_off[s]:h_off[s + 1]], t0h[s],
+                src.lam, src.beta, src.psi)
+        ref = oracle.response(*args)
+        refs.append((ref, oracle.response(*args, absval=True)))
+        data[3 * out_off[s]:3 * out_off[s + 1]] = oracle.aet(
+            ref + synth.white_noise(ref.shape, SIGMA, seed=100 + s)).ravel()
+    plan = lr.Plan(ctx, p, 1, DT, flex.gpu, t0=T0, precision=precision)
+    d = lambda a: torch.tensor(a, device="cuda:0")  # noqa: E731
+    dargs = (d(h_off), d(out_off), d(t0h), d(sky_), d(hp), d(hc), d(data))
+    xyz = torch.empty(3 * int(out_off[-1]), dtype=torch.float64, device="cuda:0")
+    got = host(plan.likelihood_batched(*dargs, weights=W, xyz=xyz))
+    plan.check()
+    xyz_h = host(xyz)
+    for s in range(len(lens)):
+        if refs[s] is None:
+            assert got[s, 0] == 0.0 and got[s, 1] == 0.0
+            continue
+        N = lens[s]
+        sl = slice(3 * out_off[s], 3 * out_off[s + 1])
+        check_against_oracle(got[s], xyz_h[sl].reshape(3, N), refs[s][0], refs[s][1], data[sl].reshape(3, N),
+                             W, p + 1, rel)
+    # deterministic: a second call gives the same bits
+    assert np.array_equal(got, host(plan.likelihood_batched(*dargs, weights=W)))
+    plan.check()
+
+
+@pytest.mark.parametrize("precision", [lr.FP64, lr.MIXED])
+def test_data_equal_to_template_gives_zero_residual(ctx, flex, precision):
+    """<d - h|d - h> = <d|d> + <h|h> - 2 <d|h> vanishes (to rounding) when d is the template."""
+    p = 25
+    N = 20000
+    src = synth.draw_sources(1, seed=3, A=1e-21, fdot=1e-17)[0]
+    t0h, hp, hc = synth.gb_input(src, T0, DT, N, p)
+    plan = lr.Plan(ctx, p, N, DT, flex.gpu, t0=T0, precision=precision)
+    xyz = host(plan.response(dev(hp), dev(hc), t0h, sky(src))).reshape(3, N)
+    data = oracle.aet(xyz)
+    dh, hh = host(plan.likelihood(dev(hp), dev(hc), t0h, sky(src), dev(data), W))
+    plan.check()
+    dd = float(np.sum(np.asarray(W)[:, None] * data * data))
+    assert abs(dd + hh - 2 * dh) <= 1e-12 * hh
+
+
+def test_data_shorter_than_offsets_is_refused_on_device(ctx, flex):
+    """n_total smaller than out_off[S]: the sources past it get NaN and the error word is set;
+    nothing past the data is read."""
+    p = 11
+    lens = [3000, 4000]
+    srcs, h_off, out_off, t0h, sky_, hp, hc = batch(lens, 7, p)
+    plan = lr.Plan(ctx, p, 1, DT, flex.gpu, t0=T0, precision=lr.MIXED)
+    d = lambda a: torch.tensor(a, device="cuda:0")  # noqa: E731
+    short = torch.zeros(3 * 5000, dtype=torch.float64, device="cuda:0")
+    got = host(plan.likelihood_batched(d(h_off), d(out_off), d(t0h), d(sky_), d(hp), d(hc), short))
+    assert np.isfinite(got[0]).all()
+    assert np.isnan(got[1]).all()
+    with pytest.raises(lr.LRError):
+        plan.check()
