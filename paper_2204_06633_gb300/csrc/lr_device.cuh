@@ -207,16 +207,17 @@ __device__ __forceinline__ void read2(const double *a, const double *b, int64_t 
 
 
 // ---------------------------------------------------------------- likelihood epilogue
-// Adds the terms of output sample n (X, Y, Z of the template) to the partial inner products
-// <d|h> and <h|h> over the channels A = (Z - X)/sqrt 2, E = (X - 2 Y + Z)/sqrt 6,
-// T = (X + Y + Z)/sqrt 3 with weights w; dat is the source's data block [3][N] in A, E, T.
-__device__ inline void like_terms(const LikeArgs &L, const double *dat, int64_t N, int64_t n, double X, double Y,
-                                  double Z, double &dh, double &hh)
+// Adds the terms of one output sample (X, Y, Z of the template; dA, dE, dT of the data) to the
+// partial inner products <d|h> and <h|h> over the channels A = (Z - X)/sqrt 2,
+// E = (X - 2 Y + Z)/sqrt 6, T = (X + Y + Z)/sqrt 3 with weights w.
+__device__ inline void like_terms(const LikeArgs &L, double X, double Y, double Z, double dA, double dE, double dT,
+                                  double &dh, double &hh)
 {
     const double R2 = 0.70710678118654752440, R6 = 0.40824829046386301637, R3 = 0.57735026918962576451;
-    const double a = (Z - X) * R2, e = (X - 2.0 * Y + Z) * R6, t = (X + Y + Z) * R3;
+    const double s = X + Z;
+    const double a = (Z - X) * R2, e = fma(-2.0, Y, s) * R6, t = (s + Y) * R3;
     const double wa = L.w[0] * a, we = L.w[1] * e, wt = L.w[2] * t;
-    dh = fma(wa, __ldg(dat + n), fma(we, __ldg(dat + N + n), fma(wt, __ldg(dat + 2 * N + n), dh)));
+    dh = fma(wa, dA, fma(we, dE, fma(wt, dT, dh)));
     hh = fma(wa, a, fma(we, e, fma(wt, t, hh)));
 }
 

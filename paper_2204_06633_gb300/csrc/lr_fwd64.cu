@@ -158,7 +158,9 @@ __global__ void __launch_bounds__(256) k_fused64(FwdParams P)
 #pragma unroll
                     for (int c = 0; c < 3; ++c) ti.out[c * ti.N + n] = o[c];
                 }
-                if (like && ti.dat) like_terms(P.like, ti.dat, ti.N, n, o[0], o[1], o[2], dh, hh);
+                if (like && ti.dat)
+                    like_terms(P.like, o[0], o[1], o[2], __ldg(ti.dat + n), __ldg(ti.dat + ti.N + n),
+                               __ldg(ti.dat + 2 * ti.N + n), dh, hh);
             }
             if (like) {
                 block_sum2(dh, hh, red);

@@ -713,11 +713,23 @@ int like_setup(lr_plan *plan, const double *weights, int64_t tiles, lr::FwdParam
         plan->lpart_cap = tiles;
     }
     P.like.data = data;
-    for (int c = 0; c < 3; ++c) P.like.w[c] = weights[c];
+    double wmax = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        P.like.w[c] = weights[c];
+        wmax = std::max(wmax, weights[c]);
+    }
+    P.like.wmax = wmax;
+    for (int c = 0; c < 3; ++c) P.like.wn[c] = wmax > 0.0 ? (float)(weights[c] / wmax) : 0.0f;
     P.like.partial = plan->d_lpart;
     P.like.cap = plan->lpart_cap;
     P.like.n_total = n_total;
     return LR_OK;
+}
+
+// the mixed epilogue sums with the weights normalised to the largest one
+double like_post(const lr_plan *plan, const lr::FwdParams &P)
+{
+    return plan->desc.precision == LR_MIXED ? P.like.wmax : 1.0;
 }
 
 }  // namespace
@@ -744,10 +756,10 @@ LR_API int lr_likelihood(lr_plan *plan, const double *hp, const double *hc, int6
     P.hp = hp;
     P.hc = hc;
     P.out = xyz;
-    st = launch_single(plan, lr::KIND_FUSED, P, stream);
+    st = launch_single(plan, lr::KIND_LIKE, P, stream);
     if (st) return st;
-    return check_launch(plan->ctx, lr::launch_like_reduce(plan->d_lpart, nullptr, tiles, 1, plan->lpart_cap, dh_hh,
-                                                          plan->d_err, stream));
+    return check_launch(plan->ctx, lr::launch_like_reduce(plan->d_lpart, nullptr, tiles, 1, plan->lpart_cap,
+                                                          like_post(plan, P), dh_hh, plan->d_err, stream));
 }
 
 LR_API int lr_likelihood_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
@@ -779,11 +791,11 @@ LR_API int lr_likelihood_batched(lr_plan *plan, int64_t S, const int64_t *h_off,
     P.hc = hc;
     P.out = xyz;
     P.total_tiles = -1;
-    st = check_launch(plan->ctx, lr::launch_forward(plan->desc.precision, lr::KIND_FUSED, plan->desc.order, P,
+    st = check_launch(plan->ctx, lr::launch_forward(plan->desc.precision, lr::KIND_LIKE, plan->desc.order, P,
                                                     plan->threads, plan->ctx->sms, stream));
     if (st) return st;
     return check_launch(plan->ctx, lr::launch_like_reduce(plan->d_lpart, plan->d_tile_off, 0, S, plan->lpart_cap,
-                                                          dh_hh, plan->d_err, stream));
+                                                          like_post(plan, P), dh_hh, plan->d_err, stream));
 }
 
 LR_API int lr_backward(lr_plan *plan, const double *hp, const double *hc, int64_t n_h, double t0_h, lr_sky sky,

@@ -84,6 +84,8 @@ struct SrcArgs {
 struct LikeArgs {
     const double *data;  // data in A, E, T: [3][N_s] per source, at 3 out_off[s] (batched)
     double w[3];         // channel weights (1 / noise variance of A, E, T)
+    double wmax;         // largest weight; wn = w / wmax in FP32 (mixed epilogue)
+    float wn[3];
     double *partial;     // [cap][2]
     int64_t cap;         // tiles the partial buffer holds
     int64_t n_total;     // samples the data array holds per channel block (sum of N_s)
@@ -156,5 +158,6 @@ inline int mx_max_tile(int HL, int HR, int lproj_b, int T)
     if (one_pass < t) t = one_pass;
     return t & ~(MX_TDI_BLOCK - 1);
 }
-enum { KIND_PROJECT = 0, KIND_TDI = 1, KIND_FUSED = 2 };
+// launch kinds: projection only, TDI only, fused, fused with the likelihood epilogue
+enum { KIND_PROJECT = 0, KIND_TDI = 1, KIND_FUSED = 2, KIND_LIKE = 3 };
 }  // namespace lr

@@ -93,10 +93,12 @@ int launch_batch_tables(const int64_t *out_off, const lr_sky *sky, int64_t S, in
 
 // Per-source sums of the likelihood partials: one warp per source adds its tiles' partials
 // (lane l takes tiles l, l + 32, ... in order, then a fixed shuffle tree), so the result does not
-// depend on the launch or on timing.  tile_off == nullptr: one source of tiles1 tiles.
+// depend on the launch or on timing; the sums are multiplied by post (the weight normalisation
+// of the mixed epilogue, 1 otherwise).  tile_off == nullptr: one source of tiles1 tiles.
 __global__ void __launch_bounds__(256) k_like_reduce(const double *__restrict__ partial,
                                                      const int64_t *__restrict__ tile_off, int64_t tiles1,
-                                                     int64_t S, int64_t cap, double *__restrict__ out, int *err)
+                                                     int64_t S, int64_t cap, double post, double *__restrict__ out,
+                                                     int *err)
 {
     const int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -119,16 +121,17 @@ __global__ void __launch_bounds__(256) k_like_reduce(const double *__restrict__ 
         hh += __shfl_down_sync(0xffffffffu, hh, o);
     }
     if (lane == 0) {
-        out[2 * s] = dh;
-        out[2 * s + 1] = hh;
+        out[2 * s] = dh * post;
+        out[2 * s + 1] = hh * post;
     }
 }
 
 int launch_like_reduce(const double *partial, const int64_t *tile_off, int64_t tiles1, int64_t S, int64_t cap,
-                       double *out, int *err, void *stream)
+                       double post, double *out, int *err, void *stream)
 {
     const int64_t blocks = (S + 7) / 8;
-    k_like_reduce<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(partial, tile_off, tiles1, S, cap, out, err);
+    k_like_reduce<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(partial, tile_off, tiles1, S, cap, post, out,
+                                                                     err);
     return (int)cudaGetLastError();
 }
 
