@@ -201,14 +201,21 @@ struct TileSetup {
     unsigned long long maxbits;
 };
 
+struct __align__(16) TermRef {
+    long long dnest;
+    int tfm;
+    float tehi;
+};
+
 struct MxShared {
     TileSetup ts[2];
     int64_t tot;     // tiles of the launch
     int64_t s_hint;  // source of the CTA's latest tile
     int unscale_e;   // exponent of the inverse of the current tile's power-of-two scale
     // TDI reference per delayed term (current tile)
-    int tfm[NTERM];
-    float tehi[NTERM];
+    // per delayed term: nested minus summed total delay at the reference output (fixed point,
+    // constant over a tile; 0 for summed delays), the reference index offset and fraction
+    TermRef tref[NTERM];
     float redf[2 * (MIXED_THREADS / 32)];  // likelihood block sums
 };
 
@@ -662,10 +669,23 @@ __device__ void tdi_refs(const FwdParams &P, const TileSetup &ts, MxShared &sh, 
     const int iv = ts.ic < ts.jswt ? 0 : 1;
     long long D = 0;
     for (int k = 1; k <= q; ++k) D += ts.dp[iv][c_tdimx.pair[ch][c][k]].Xc;
+    // nested chained delays: the nested minus summed total delay of the term at the reference
+    // output, interpolated in the plan's knot table (it changes by < 1e-10 samples over a tile,
+    // so one value serves the tile; the reference split keeps the summed delay, ~1e-7 samples
+    // away: at worst an item leaves the fast path)
+    long long dn = 0;
+    if (P.nest_tab) {
+        const double u = (P.t0 + (double)(ts.ti.n0 + ts.ic) * P.dt - P.nest_t0) * P.nest_inv_dk;
+        const int k = u <= 0.0 ? 0 : (u >= (double)(P.nest_n - 2) ? P.nest_n - 2 : (int)u);
+        const double f = fmin(fmax(u - (double)k, 0.0), 1.0);
+        const double a = __ldg(P.nest_tab + k * NTERM + id), b = __ldg(P.nest_tab + (k + 1) * NTERM + id);
+        dn = llrint(fma(f, b - a, a) * (double)(1ll << FX_BITS));
+    }
+    sh.tref[id].dnest = dn;
     const int nlr = ts.ic + P.HL;
     const Split s = split_fx(((long long)nlr << FX_BITS) - D);
-    sh.tfm[id] = s.m - nlr;
-    sh.tehi[id] = s.ehi;
+    sh.tref[id].tfm = s.m - nlr;
+    sh.tref[id].tehi = s.ehi;
     constexpr int NUP = mx_nup(T);
     float2 *w = reinterpret_cast<float2 *>(tw) + id * NUP;
     if constexpr (T >= 4) {
@@ -1029,14 +1049,16 @@ __device__ __forceinline__ void tdi_chain(const FwdParams &P, const MxShared &sh
         dk[1] += dv.y;
         dk[2] += dv.z;
         dk[3] += dv.w;
-        const Split s0 = split_fx(((long long)nl0 << FX_BITS) - D0);
+        const TermRef tr = sh.tref[id];
+        const long long Dq = D0 + tr.dnest;  // the term's delay at output i0
+        const Split s0 = split_fx(((long long)nl0 << FX_BITS) - Dq);
         const int m0 = s0.m;
         const float eh = s0.ehi;
         float el[TB];
         el[0] = s0.elo;
 #pragma unroll
         for (int k = 1; k < TB; ++k) el[k] = fmaf(-dk[k], 0x1p-44f, s0.elo);
-        bool fast = (m0 - nl0 == sh.tfm[id]) && (m0 - h >= 0) && (m0 + kmax + h < ny);
+        bool fast = (m0 - nl0 == tr.tfm) && (m0 - h >= 0) && (m0 + kmax + h < ny);
 #pragma unroll
         for (int k = 1; k < TB; ++k) fast = fast && (k >= kmax || (eh + el[k] >= 0.0f && eh + el[k] < 1.0f));
         const int yb = ybase(lk);
@@ -1050,7 +1072,7 @@ __device__ __forceinline__ void tdi_chain(const FwdParams &P, const MxShared &sh
 #pragma unroll
             for (int k = 0; k < TB; ++k) C[k] = 0.0f;
             if constexpr (T >= 4) {
-                const float dref = eh - sh.tehi[id];
+                const float dref = eh - tr.tehi;
                 // (e, e) pairs of the window in a ring of RW: taps a, a+1 read e[a .. a+TB]
                 constexpr int RW = TB + 2;
                 unsigned long long win[RW];
@@ -1100,7 +1122,7 @@ __device__ __forceinline__ void tdi_chain(const FwdParams &P, const MxShared &sh
 #pragma unroll
             for (int k = 0; k < TB; ++k) {
                 if (k < kmax) {
-                    const Split sk = split_fx(((long long)(nl0 + k) << FX_BITS) - (D0 + (long long)dk[k]));
+                    const Split sk = split_fx(((long long)(nl0 + k) << FX_BITS) - (Dq + (long long)dk[k]));
                     float r[6];
                     tdi_read_exact<T>(smf, lk, sk.m, sk.ehi, sk.elo, ny, P.err, r);
                     float hk = lane(HI[k >> 1], k & 1), lk_ = lane(LO[k >> 1], k & 1), sk_ = lane(SM[k >> 1], k & 1);

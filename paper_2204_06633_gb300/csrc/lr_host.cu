@@ -14,6 +14,7 @@
 #include "lr_launch.h"
 #include "lr_pipeline.h"
 #include "lr_planview.h"
+#include "lr_tdi_table.cuh"
 
 struct lr_ctx {
     int device;
@@ -55,6 +56,8 @@ struct lr_plan {
     // per-tile likelihood partials
     double *d_lpart;
     int64_t lpart_cap;
+    // nested-delay table of the mixed kernels ([knots][42], samples)
+    double *d_nest;
 };
 
 namespace lr {
@@ -217,6 +220,44 @@ void chebyshev_inverse(double out[4][4], double node[4])
     // a[:, 4:] = V^{-1}: coefficient k = sum_i V^{-1}[k][i] y_i
     for (int k = 0; k < 4; ++k)
         for (int i = 0; i < 4; ++i) out[k][i] = a[k][4 + i];
+}
+
+// Nested chained delays for the mixed kernels (Sec. TDI, the chained delay with each L taken at
+// the time the light left: t_k = t_{k-1} - L(t_{k-1})): at every knot t of the TDI orbit and
+// for every delayed term (channel, chain, q), the nested total delay minus the summed one
+// (all L at t), in samples.  The difference is smooth on orbital time scales (~1e-7 samples,
+// second derivative ~1e-20 s/s^2), so the kernels interpolate it linearly per tile.
+int nested_table(lr_plan *p, const lr_orbit *o)
+{
+    const lr::TdiTab tab = lr::make_tdi_tab();
+    const int nk = o->nint + 1;
+    std::vector<double> h((size_t)nk * 42, 0.0);
+    for (int k = 0; k < nk; ++k) {
+        const double t = o->t_first + (double)k * o->dk;
+        for (int ch = 0; ch < 3; ++ch)
+            for (int c = 0; c < 2; ++c) {
+                double Dn = 0.0, Ds = 0.0;
+                for (int q = 1; q <= 7; ++q) {
+                    const int l = tab.pair[ch][c][q];
+                    Dn += spline_eval_host(o, 9 + l, t - Dn);
+                    Ds += spline_eval_host(o, 9 + l, t);
+                    h[(size_t)k * 42 + (ch * 2 + c) * 7 + q - 1] = (Dn - Ds) / p->desc.dt;
+                }
+            }
+    }
+    cudaError_t e = lr::dev_malloc((void **)&p->d_nest, sizeof(double) * h.size());
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_nest, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (p->d_nest) cudaFree(p->d_nest);
+        p->d_nest = nullptr;
+        return cuda_fail(p->ctx, e);
+    }
+    lr::FwdParams &P = p->base;
+    P.nest_tab = p->d_nest;
+    P.nest_n = nk;
+    P.nest_t0 = o->t_first;
+    P.nest_inv_dk = 1.0 / o->dk;
+    return LR_OK;
 }
 
 bool all_finite(const double *p, size_t n)
@@ -441,6 +482,7 @@ LR_API int lr_plan_create(lr_ctx *ctx, const lr_plan_desc *d, lr_plan **out)
     p->pipe = nullptr;
     p->d_lpart = nullptr;
     p->lpart_cap = 0;
+    p->d_nest = nullptr;
     lr::FwdParams &P = p->base;
     std::memset(&P, 0, sizeof(P));
     P.dt = d->dt;
@@ -483,11 +525,7 @@ LR_API int lr_plan_create(lr_ctx *ctx, const lr_plan_desc *d, lr_plan **out)
     P.wmax = P.ymax + 2 * P.sig_b + P.lproj_b + p->T + 4;
     if (d->precision == LR_MIXED) {
         // the mixed kernels re-expand the orbit cubics over a tile: a tile's link span must fit
-        // in two knot intervals, and the chained delays are summed, not nested
-        if (d->delay_mode == LR_DELAY_NESTED) {
-            delete p;
-            return LR_ERR_UNSUPPORTED;
-        }
+        // in two knot intervals
         if ((double)P.ymax * d->dt >= d->proj_orbit->dk || (double)P.tile * d->dt >= d->tdi_orbit->dk) {
             delete p;
             return LR_ERR_RANGE;
@@ -502,6 +540,14 @@ LR_API int lr_plan_create(lr_ctx *ctx, const lr_plan_desc *d, lr_plan **out)
         return cuda_fail(ctx, e);
     }
     P.err = p->d_err;
+    if (d->precision == LR_MIXED && d->delay_mode == LR_DELAY_NESTED) {
+        const int st = nested_table(p, d->tdi_orbit);
+        if (st) {
+            cudaFree(p->d_err);
+            delete p;
+            return st;
+        }
+    }
     *out = p;
     return LR_OK;
 }
@@ -516,6 +562,7 @@ LR_API int lr_plan_destroy(lr_plan *plan)
     if (plan->d_ktile_off) cudaFree(plan->d_ktile_off);
     if (plan->d_htile_off) cudaFree(plan->d_htile_off);
     if (plan->d_lpart) cudaFree(plan->d_lpart);
+    if (plan->d_nest) cudaFree(plan->d_nest);
     lr::pipe_free(plan->pipe);
     delete plan;
     return LR_OK;

@@ -110,6 +110,12 @@ struct FwdParams {
     LikeArgs like;
     int *err;               // device error word
     int64_t total_tiles;    // >= 0 single source; -1: read src.tile_off[S]
+    // nested chained delays in the mixed kernels: per delayed term (42) the nested minus the
+    // summed total delay (samples) at the TDI orbit's knots, interpolated linearly per tile;
+    // null for summed delays
+    const double *nest_tab;  // [nest_n][42]
+    int nest_n;
+    double nest_t0, nest_inv_dk;
     double cheb[4][4];      // monomial coefficients of the cubic through 4 Chebyshev nodes on [-1, 1]
     double cheb_node[4];    // the nodes cos((2 i + 1) pi / 8)
 };

@@ -40,8 +40,7 @@ def test_plan_arguments_refused_on_host(ctx, orbit):
     assert status_of(lambda: lr.Plan(ctx, 25, 0, DT, orbit)) == INVALID
     assert status_of(lambda: lr.Plan(ctx, 25, 100, -1.0, orbit)) == INVALID
     assert status_of(lambda: lr.Plan(ctx, 25, 100, DT, orbit, generation=3)) == INVALID
-    assert status_of(lambda: lr.Plan(ctx, 25, 100, DT, orbit, precision=lr.MIXED,
-                                     delay_mode=lr.DELAY_NESTED)) == UNSUPPORTED
+    assert status_of(lambda: lr.Plan(ctx, 25, 100, DT, orbit, delay_mode=2)) == INVALID
 
 
 def test_orbit_arguments_refused_on_host(ctx):
