@@ -34,6 +34,23 @@ def test_config1_plain_method_fp64(ctx):
         assert e < REL64, f"{kind}: {e:.3e}"
 
 
+@pytest.mark.parametrize("precision,rel", [(lr.FP64, REL64), (lr.MIXED, 1e-6)])
+def test_config1_against_stored_fixture(ctx, precision, rel):
+    """The plain-method workload at the indices of tests/golden/config1_xyz.txt (oracle values
+    written by tests/golden/make_golden.py)."""
+    import os
+    fx = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "config1_xyz.txt"))
+    idx, ref = fx[:, 0].astype(np.int64), fx[:, 1:].T
+    src = synth.config1_source()
+    N, p = 65536, 25
+    t0h, hp, hc = synth.gb_input(src, T0, DT, N, p)
+    o = synth.orbit_static(-2e5, N * DT + 2e5)
+    plan = lr.Plan(ctx, p, N, DT, lr.Orbit(ctx, o.t_knots, o.pos, o.delays), t0=T0, precision=precision)
+    got = host(plan.response(dev(hp), dev(hc), t0h, sky(src)))[:, idx]
+    plan.check()
+    assert np.linalg.norm(got - ref) <= rel * np.linalg.norm(ref)
+
+
 @pytest.mark.parametrize("p", [1, 3, 5, 11, 25, 41])
 def test_orders_static_ragged(ctx, p):
     src = synth.config1_source()
