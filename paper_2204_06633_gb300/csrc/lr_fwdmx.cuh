@@ -22,6 +22,10 @@
 //           one compensated accumulator; each delayed read uses the tile reference weights and
 //           their derivative (a first-order expansion in the fraction, which drifts by ~1e-7 per
 //           sample), a register window of third differences and a float-float anchor.
+//           Nested chained delays add a per-tile constant per term (nested minus summed delay,
+//           from the plan's knot table).
+//  like     (KIND_LIKE only) A, E, T of the tile against the data, fetched by cp.async during
+//           the TDI phase; FP32 products on the tile-scaled values, a fixed-order block sum.
 // Reads whose integer index does not follow the item's pattern (an index step inside an item,
 // a knot of the orbit spline inside a projection item) take an exact per-sample path.
 #pragma once
