@@ -34,7 +34,7 @@ def _worker(rank, ws, port, out):
 @pytest.mark.timeout(120)
 def test_two_rank_job_throughput():
     ws, port = 2, _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(ws, port, out), nprocs=ws, join=True)
     r0, r1 = out[0], out[1]
