@@ -252,6 +252,22 @@ LR_API int lr_likelihood_batched(lr_plan *plan, int64_t S, const int64_t *h_off,
                                  const double *data, int64_t n_total, const double *weights, double *dh_hh,
                                  double *xyz, void *stream);
 
+/* Gradient of the time-domain log-likelihood (up to the constant -<d|d>/2),
+ * <d|h> - <h|h>/2 over A, E, T with the weights of lr_likelihood, with respect to the template's
+ * X, Y, Z: g_xyz = scale * M^T W (data - M xyz), M the A, E, T map, W = diag(weights).  Feed
+ * g_xyz to lr_backward for the gradient with respect to h+, hx and the sky angles.
+ *   xyz, data, g_xyz : DEVICE [3][plan.n] (X, Y, Z; A, E, T; X, Y, Z); g_xyz may alias neither.
+ *   weights : HOST double[3] (finite, >= 0); scale: host factor (e.g. the upstream gradient).
+ * Elementwise, FP64 in both plan precisions.  LR_ERR_INVALID_ARG for null pointers or bad
+ * weights, LR_ERR_NONFINITE for a non-finite scale. */
+LR_API int lr_likelihood_grad(lr_plan *plan, const double *xyz, const double *data, const double *weights,
+                              double scale, double *g_xyz, void *stream);
+/* Batched form: out_off DEVICE int64[S+1] as lr_response_batched (source s at 3*out_off[s] as
+ * [3][n_s] in xyz, data and g_xyz); S <= 2^24; decreasing offsets record LR_ERR_DEVICE. */
+LR_API int lr_likelihood_grad_batched(lr_plan *plan, int64_t S, const int64_t *out_off, const double *xyz,
+                                      const double *data, const double *weights, double scale, double *g_xyz,
+                                      void *stream);
+
 /* Batched transpose; g_sky is DEVICE [S][3] (may be NULL). */
 LR_API int lr_backward_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
                                const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,

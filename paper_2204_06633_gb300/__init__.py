@@ -74,6 +74,8 @@ _SIGS = {
     "lr_plan_autotune": (_I, [_P, _I64, _I, _P, ctypes.POINTER(_I)]),
     "lr_likelihood": (_I, [_P, _P, _P, _I64, _D, lr_sky, _P, _P, _P, _P, _P]),
     "lr_likelihood_batched": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _P, _P, _P]),
+    "lr_likelihood_grad": (_I, [_P, _P, _P, _P, _D, _P, _P]),
+    "lr_likelihood_grad_batched": (_I, [_P, _I64, _P, _P, _P, _P, _D, _P, _P]),
 }
 NOALLOC_MAX_SOURCES = 65536
 
@@ -313,6 +315,27 @@ class Plan:
             _dev64(xyz, "xyz", 3 * n_total) if xyz is not None else None, _stream_handle(stream)))
         return out
 
+    def likelihood_grad(self, xyz, data, weights=(1.0, 1.0, 1.0), scale=1.0, g_xyz=None, stream=None):
+        """d(<d|h> - <h|h>/2)/d(X, Y, Z) times scale, float64 CUDA [3][n], from the template's X, Y, Z
+        and the data in A, E, T (both float64 CUDA [3][n])."""
+        g_xyz = self._out(g_xyz, (3, self.n), xyz)
+        w = (ctypes.c_double * 3)(*[float(x) for x in weights])
+        _check("lr_likelihood_grad", library().lr_likelihood_grad(
+            self._h, _dev64(xyz, "xyz", 3 * self.n), _dev64(data, "data", 3 * self.n), ctypes.addressof(w),
+            float(scale), _dev64(g_xyz, "g_xyz", 3 * self.n), _stream_handle(stream)))
+        return g_xyz
+
+    def likelihood_grad_batched(self, out_off, xyz, data, weights=(1.0, 1.0, 1.0), scale=1.0, g_xyz=None,
+                                stream=None):
+        """Batched likelihood_grad: xyz, data, g_xyz packed like the batched X, Y, Z."""
+        S = out_off.numel() - 1
+        g_xyz = self._out(g_xyz, (xyz.numel(),), xyz)
+        w = (ctypes.c_double * 3)(*[float(x) for x in weights])
+        _check("lr_likelihood_grad_batched", library().lr_likelihood_grad_batched(
+            self._h, S, _devi64(out_off, "out_off", S + 1), _dev64(xyz, "xyz"), _dev64(data, "data", xyz.numel()),
+            ctypes.addressof(w), float(scale), _dev64(g_xyz, "g_xyz", xyz.numel()), _stream_handle(stream)))
+        return g_xyz
+
     def response_batched_host(self, h_off, out_off, t0h, sky, hp, hc, xyz=None, stream=None):
         """The batched response on host arrays (numpy or CPU tensors; page-locked tensors let
         the copies overlap the kernels): chunks of sources are copied in, computed and copied
@@ -421,3 +444,32 @@ def response(plan: Plan, hp, hc, sky, t0h: float):
     if not isinstance(sky, torch.Tensor):
         sky = torch.tensor(sky, dtype=torch.float64, device=hp.device)
     return _Response.apply(hp, hc, sky, plan, t0h)
+
+
+class _LogLikelihood(torch.autograd.Function):
+    """<d|h> - <h|h>/2 over A, E, T (the log-likelihood up to -<d|d>/2) with the fused likelihood
+    kernel forward and the likelihood gradient + the library's adjoint as backward."""
+
+    @staticmethod
+    def forward(ctx, hp, hc, sky, plan, t0h, data, weights):
+        s = tuple(float(v) for v in sky.detach().cpu().tolist())
+        xyz = torch.empty((3, plan.n), dtype=torch.float64, device=hp.device)
+        dh_hh = plan.likelihood(hp.contiguous(), hc.contiguous(), t0h, s, data, weights, xyz=xyz)
+        ctx.plan, ctx.t0h, ctx.sky, ctx.weights = plan, t0h, s, weights
+        ctx.save_for_backward(hp, hc, xyz, data)
+        return dh_hh[0] - 0.5 * dh_hh[1]
+
+    @staticmethod
+    def backward(ctx, g):
+        hp, hc, xyz, data = ctx.saved_tensors
+        g_xyz = ctx.plan.likelihood_grad(xyz, data, ctx.weights, scale=float(g))
+        g_hp, g_hc, g_sky = ctx.plan.backward(hp.contiguous(), hc.contiguous(), ctx.t0h, ctx.sky, g_xyz)
+        return g_hp, g_hc, g_sky.to(hp.device), None, None, None, None
+
+
+def log_likelihood(plan: Plan, hp, hc, sky, t0h: float, data, weights=(1.0, 1.0, 1.0)):
+    """Differentiable <d|h> - <h|h>/2 (A, E, T channels, white noise of variance 1/w_c): gradients
+    flow to h+, hx and sky = (lambda, beta, psi); data is float64 CUDA [3][n] in A, E, T."""
+    if not isinstance(sky, torch.Tensor):
+        sky = torch.tensor(sky, dtype=torch.float64, device=hp.device)
+    return _LogLikelihood.apply(hp, hc, sky, plan, t0h, data, tuple(float(x) for x in weights))

@@ -126,6 +126,47 @@ __global__ void __launch_bounds__(256) k_like_reduce(const double *__restrict__ 
     }
 }
 
+// Gradient of the time-domain log-likelihood <d|h> - <h|h>/2 (A, E, T channels, weights w) with
+// respect to the template's X, Y, Z: g = scale * M^T W (d - M x), M the A, E, T map (rows
+// (-1, 0, 1)/sqrt 2, (1, -2, 1)/sqrt 6, (1, 1, 1)/sqrt 3).  Source s (of S) holds [3][N_s] at
+// 3 out_off[s] in x, d and g; out_off == nullptr: one source of n1 samples.  Blocks walk sources,
+// threads walk samples.
+__global__ void __launch_bounds__(256) k_like_grad(const int64_t *__restrict__ out_off, int64_t S, int64_t n1,
+                                                   const double *__restrict__ x, const double *__restrict__ d,
+                                                   double w0, double w1, double w2, double scale,
+                                                   double *__restrict__ g, int *err)
+{
+    const double R2 = 0.70710678118654752440, R6 = 0.40824829046386301637, R3 = 0.57735026918962576451;
+    for (int64_t s = blockIdx.x; s < S; s += gridDim.x) {
+        const int64_t o = out_off ? out_off[s] : 0, N = out_off ? out_off[s + 1] - o : n1;
+        if (N < 0) {
+            if (threadIdx.x == 0) atomicOr(err, ERR_OFFSETS);
+            continue;
+        }
+        const double *xs = x + 3 * o, *ds = d + 3 * o;
+        double *gs = g + 3 * o;
+        for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+            const double X = xs[i], Y = xs[N + i], Z = xs[2 * N + i];
+            const double s2 = X + Z;
+            const double ra = w0 * (ds[i] - (Z - X) * R2), re = w1 * (ds[N + i] - fma(-2.0, Y, s2) * R6),
+                         rt = w2 * (ds[2 * N + i] - (s2 + Y) * R3);
+            const double e6 = re * R6, t3 = rt * R3;
+            gs[i] = scale * (fma(-ra, R2, e6) + t3);
+            gs[N + i] = scale * fma(-2.0, e6, t3);
+            gs[2 * N + i] = scale * (fma(ra, R2, e6) + t3);
+        }
+    }
+}
+
+int launch_like_grad(const int64_t *out_off, int64_t S, int64_t n1, const double *x, const double *d,
+                     const double *w, double scale, double *g, int *err, void *stream)
+{
+    const int64_t blocks = S < 4096 ? S : 4096;
+    k_like_grad<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(out_off, S, n1, x, d, w[0], w[1], w[2], scale, g,
+                                                                   err);
+    return (int)cudaGetLastError();
+}
+
 int launch_like_reduce(const double *partial, const int64_t *tile_off, int64_t tiles1, int64_t S, int64_t cap,
                        double post, double *out, int *err, void *stream)
 {

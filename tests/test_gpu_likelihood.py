@@ -219,3 +219,85 @@ def test_bench_workload_sampled(ctx):
                                  p + 1, 1e-6, lr.MIXED)
         else:
             check_epilogue(got[s], xs, ds, W, lr.MIXED)
+
+
+def aet_matrix():
+    """The A, E, T map as a 3x3 matrix, column j = the oracle's A, E, T of the unit X, Y, Z
+    pattern j."""
+    return np.stack([oracle.aet(np.eye(3)[:, j].reshape(3, 1))[:, 0] for j in range(3)], axis=1)
+
+
+@pytest.mark.parametrize("scale", [1.0, -0.37])
+def test_likelihood_grad_against_the_oracle_map(ctx, flex, scale):
+    """g = scale M^T W (d - M x) per sample, single source and a ragged batch with an empty
+    source (M from the oracle's A, E, T; a plain matrix product on the host)."""
+    M = aet_matrix()
+    rng = np.random.default_rng(21)
+    w = (2.0, 0.5, 1.25)
+    plan = lr.Plan(ctx, 11, 1000, DT, flex.gpu, t0=T0)
+    x, dat = rng.normal(size=(3, 1000)), rng.normal(size=(3, 1000))
+    got = host(plan.likelihood_grad(dev(x), dev(dat), w, scale=scale))
+    ref = scale * M.T @ (np.asarray(w)[:, None] * (dat - M @ x))
+    assert np.linalg.norm(got - ref) <= 1e-14 * np.linalg.norm(ref)
+    lens = [700, 0, 1, 2500]
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    xb, db = rng.normal(size=3 * off[-1]), rng.normal(size=3 * off[-1])
+    gb = host(plan.likelihood_grad_batched(torch.tensor(off, device="cuda:0"), dev(xb), dev(db), w, scale=scale))
+    plan.check()
+    for s, n in enumerate(lens):
+        sl = slice(3 * off[s], 3 * off[s + 1])
+        r = scale * M.T @ (np.asarray(w)[:, None] * (db[sl].reshape(3, n) - M @ xb[sl].reshape(3, n)))
+        assert np.allclose(gb[sl].reshape(3, n), r, rtol=0, atol=1e-14 * max(1.0, np.abs(r).max()))
+
+
+@pytest.mark.parametrize("precision", [lr.FP64, lr.MIXED])
+def test_log_likelihood_autograd(ctx, flex, precision):
+    """Gradients of <d|h> - <h|h>/2 through lr.log_likelihood: against autograd through the fused
+    response with the loss written in PyTorch (same adjoint, independent likelihood gradient),
+    and, in FP64, against central differences (exact for h: the loss is quadratic in h; step 1e-6
+    relative for the sky angles, agreement 1e-6)."""
+    p, N = 11, 4000
+    src = synth.draw_sources(1, seed=8, A=1e-21, fdot=1e-17)[0]
+    t0h, hp, hc = synth.gb_input(src, T0, DT, N, p)
+    plan = lr.Plan(ctx, p, N, DT, flex.gpu, t0=T0, precision=precision)
+    xyz0 = host(plan.response(dev(hp), dev(hc), t0h, sky(src))).reshape(3, N)
+    data = dev(oracle.aet(xyz0 + synth.white_noise(xyz0.shape, SIGMA, seed=4)))
+    M = torch.tensor(aet_matrix(), device="cuda:0")
+    wt = torch.tensor(W, device="cuda:0")[:, None]
+
+    def run(fn):
+        a = dev(hp).requires_grad_()
+        b = dev(hc).requires_grad_()
+        s = torch.tensor(sky(src), dtype=torch.float64, device="cuda:0", requires_grad=True)
+        L = fn(a, b, s)
+        L.backward()
+        return float(L), host(a.grad), host(b.grad), host(s.grad)
+
+    L1, gp1, gc1, gs1 = run(lambda a, b, s: lr.log_likelihood(plan, a, b, s, t0h, data, W))
+
+    def torch_loss(a, b, s):
+        h = M @ lr.response(plan, a, b, s, t0h)
+        return torch.sum(wt * (data * h - 0.5 * h * h))
+
+    L2, gp2, gc2, gs2 = run(torch_loss)
+    plan.check()
+    tol = 1e-12 if precision == lr.FP64 else 1e-5
+    assert abs(L1 - L2) <= tol * abs(L2)
+    for g1, g2 in ((gp1, gp2), (gc1, gc2), (gs1, gs2)):
+        assert np.linalg.norm(g1 - g2) <= 1e-12 * np.linalg.norm(g2)
+    if precision == lr.FP64:
+        rng = np.random.default_rng(5)
+        v = rng.normal(size=hp.shape) * np.abs(hp).max()
+
+        def L_at(a, s=sky(src)):
+            return float(lr.log_likelihood(plan, dev(a), dev(hc), tuple(s), t0h, data, W))
+
+        fd = (L_at(hp + v) - L_at(hp - v)) / 2.0
+        assert abs(fd - float(np.dot(gp1, v))) <= 1e-9 * abs(fd)
+        for i in range(3):
+            e = 1e-6 * max(1.0, abs(sky(src)[i]))
+            sp, sm = list(sky(src)), list(sky(src))
+            sp[i] += e
+            sm[i] -= e
+            fds = (L_at(hp, tuple(sp)) - L_at(hp, tuple(sm))) / (2 * e)
+            assert abs(fds - gs1[i]) <= 1e-6 * np.linalg.norm(gs1)
