@@ -263,10 +263,11 @@ LR_API int lr_likelihood_batched(lr_plan *plan, int64_t S, const int64_t *h_off,
 LR_API int lr_likelihood_grad(lr_plan *plan, const double *xyz, const double *data, const double *weights,
                               double scale, double *g_xyz, void *stream);
 /* Batched form: out_off DEVICE int64[S+1] as lr_response_batched (source s at 3*out_off[s] as
- * [3][n_s] in xyz, data and g_xyz); S <= 2^24; decreasing offsets record LR_ERR_DEVICE. */
-LR_API int lr_likelihood_grad_batched(lr_plan *plan, int64_t S, const int64_t *out_off, const double *xyz,
-                                      const double *data, const double *weights, double scale, double *g_xyz,
-                                      void *stream);
+ * [3][n_s] in xyz, data and g_xyz, which hold n_total samples per channel block); S <= 2^24.
+ * Sources whose offsets decrease or run past n_total are skipped and record LR_ERR_DEVICE. */
+LR_API int lr_likelihood_grad_batched(lr_plan *plan, int64_t S, const int64_t *out_off, int64_t n_total,
+                                      const double *xyz, const double *data, const double *weights, double scale,
+                                      double *g_xyz, void *stream);
 
 /* Batched transpose; g_sky is DEVICE [S][3] (may be NULL). */
 LR_API int lr_backward_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,

@@ -75,7 +75,7 @@ _SIGS = {
     "lr_likelihood": (_I, [_P, _P, _P, _I64, _D, lr_sky, _P, _P, _P, _P, _P]),
     "lr_likelihood_batched": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _P, _P, _P]),
     "lr_likelihood_grad": (_I, [_P, _P, _P, _P, _D, _P, _P]),
-    "lr_likelihood_grad_batched": (_I, [_P, _I64, _P, _P, _P, _P, _D, _P, _P]),
+    "lr_likelihood_grad_batched": (_I, [_P, _I64, _P, _I64, _P, _P, _P, _D, _P, _P]),
 }
 NOALLOC_MAX_SOURCES = 65536
 
@@ -329,10 +329,13 @@ class Plan:
                                 stream=None):
         """Batched likelihood_grad: xyz, data, g_xyz packed like the batched X, Y, Z."""
         S = out_off.numel() - 1
+        if xyz.numel() % 3:
+            raise ValueError("xyz must hold three channel blocks")
         g_xyz = self._out(g_xyz, (xyz.numel(),), xyz)
         w = (ctypes.c_double * 3)(*[float(x) for x in weights])
         _check("lr_likelihood_grad_batched", library().lr_likelihood_grad_batched(
-            self._h, S, _devi64(out_off, "out_off", S + 1), _dev64(xyz, "xyz"), _dev64(data, "data", xyz.numel()),
+            self._h, S, _devi64(out_off, "out_off", S + 1), xyz.numel() // 3, _dev64(xyz, "xyz"),
+            _dev64(data, "data", xyz.numel()),
             ctypes.addressof(w), float(scale), _dev64(g_xyz, "g_xyz", xyz.numel()), _stream_handle(stream)))
         return g_xyz
 

@@ -848,20 +848,21 @@ LR_API int lr_likelihood_batched(lr_plan *plan, int64_t S, const int64_t *h_off,
 LR_API int lr_likelihood_grad(lr_plan *plan, const double *xyz, const double *data, const double *weights,
                               double scale, double *g_xyz, void *stream)
 {
-    return lr_likelihood_grad_batched(plan, 1, nullptr, xyz, data, weights, scale, g_xyz, stream);
+    if (!plan) return LR_ERR_INVALID_ARG;
+    return lr_likelihood_grad_batched(plan, 1, nullptr, plan->desc.n, xyz, data, weights, scale, g_xyz, stream);
 }
 
-LR_API int lr_likelihood_grad_batched(lr_plan *plan, int64_t S, const int64_t *out_off, const double *xyz,
-                                      const double *data, const double *weights, double scale, double *g_xyz,
-                                      void *stream)
+LR_API int lr_likelihood_grad_batched(lr_plan *plan, int64_t S, const int64_t *out_off, int64_t n_total,
+                                      const double *xyz, const double *data, const double *weights, double scale,
+                                      double *g_xyz, void *stream)
 {
     if (!plan || !xyz || !data || !weights || !g_xyz) return LR_ERR_INVALID_ARG;
-    if (S < 1 || (!out_off && S != 1)) return LR_ERR_INVALID_ARG;
+    if (S < 1 || n_total < 0 || (!out_off && S != 1)) return LR_ERR_INVALID_ARG;
     if (S > (int64_t)1 << 24) return LR_ERR_RANGE;
     for (int c = 0; c < 3; ++c)
         if (!std::isfinite(weights[c]) || weights[c] < 0.0) return LR_ERR_INVALID_ARG;
     if (!std::isfinite(scale)) return LR_ERR_NONFINITE;
-    return check_launch(plan->ctx, lr::launch_like_grad(out_off, S, plan->desc.n, xyz, data, weights, scale, g_xyz,
+    return check_launch(plan->ctx, lr::launch_like_grad(out_off, S, n_total, xyz, data, weights, scale, g_xyz,
                                                         plan->d_err, stream));
 }
 

@@ -129,7 +129,8 @@ __global__ void __launch_bounds__(256) k_like_reduce(const double *__restrict__ 
 // Gradient of the time-domain log-likelihood <d|h> - <h|h>/2 (A, E, T channels, weights w) with
 // respect to the template's X, Y, Z: g = scale * M^T W (d - M x), M the A, E, T map (rows
 // (-1, 0, 1)/sqrt 2, (1, -2, 1)/sqrt 6, (1, 1, 1)/sqrt 3).  Source s (of S) holds [3][N_s] at
-// 3 out_off[s] in x, d and g; out_off == nullptr: one source of n1 samples.  Blocks walk sources,
+// 3 out_off[s] in x, d and g, which hold n1 samples per channel block (sources past them are
+// skipped and recorded); out_off == nullptr: one source of n1 samples.  Blocks walk sources,
 // threads walk samples.
 __global__ void __launch_bounds__(256) k_like_grad(const int64_t *__restrict__ out_off, int64_t S, int64_t n1,
                                                    const double *__restrict__ x, const double *__restrict__ d,
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(256) k_like_grad(const int64_t *__restrict__ o
     const double R2 = 0.70710678118654752440, R6 = 0.40824829046386301637, R3 = 0.57735026918962576451;
     for (int64_t s = blockIdx.x; s < S; s += gridDim.x) {
         const int64_t o = out_off ? out_off[s] : 0, N = out_off ? out_off[s + 1] - o : n1;
-        if (N < 0) {
+        if (N < 0 || o < 0 || o + N > n1) {
             if (threadIdx.x == 0) atomicOr(err, ERR_OFFSETS);
             continue;
         }

@@ -13,7 +13,8 @@ int launch_tile_offsets(const int64_t *out_off, int64_t S, int tile, int64_t *ti
 int launch_batch_tables(const int64_t *out_off, const lr_sky *sky, int64_t S, int tile, int64_t *tile_off,
                         SkyConst *skyc, int *err, void *stream);
 bool order_compiled(int order);
-// g = scale * d(<d|h> - <h|h>/2)/d(X, Y, Z) per sample (out_off == nullptr: one source of n1)
+// g = scale * d(<d|h> - <h|h>/2)/d(X, Y, Z) per sample; the arrays hold n1 samples per channel
+// block (out_off == nullptr: one source of n1)
 int launch_like_grad(const int64_t *out_off, int64_t S, int64_t n1, const double *x, const double *d,
                      const double *w, double scale, double *g, int *err, void *stream);
 // per-source (<d|h>, <h|h>) from the per-tile partials of a likelihood launch, times post

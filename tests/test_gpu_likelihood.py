@@ -301,3 +301,15 @@ def test_log_likelihood_autograd(ctx, flex, precision):
             sm[i] -= e
             fds = (L_at(hp, tuple(sp)) - L_at(hp, tuple(sm))) / (2 * e)
             assert abs(fds - gs1[i]) <= 1e-6 * np.linalg.norm(gs1)
+
+
+def test_likelihood_grad_batched_refuses_offsets_past_the_arrays(ctx, flex):
+    plan = lr.Plan(ctx, 11, 1000, DT, flex.gpu, t0=T0)
+    off = torch.tensor([0, 700, 1400], dtype=torch.int64, device="cuda:0")
+    x = torch.ones(3 * 1000, dtype=torch.float64, device="cuda:0")
+    g = torch.full_like(x, 7.0)
+    plan.likelihood_grad_batched(off, x, x.clone(), (1.0, 1.0, 1.0), g_xyz=g)
+    torch.cuda.synchronize()
+    assert torch.all(g[2100:] == 7.0)  # the second source is not touched ...
+    with pytest.raises(lr.LRError):    # ... and the error word says why
+        plan.check()
