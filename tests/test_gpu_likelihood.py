@@ -247,7 +247,7 @@ def test_likelihood_grad_against_the_oracle_map(ctx, flex, scale):
     for s, n in enumerate(lens):
         sl = slice(3 * off[s], 3 * off[s + 1])
         r = scale * M.T @ (np.asarray(w)[:, None] * (db[sl].reshape(3, n) - M @ xb[sl].reshape(3, n)))
-        assert np.allclose(gb[sl].reshape(3, n), r, rtol=0, atol=1e-14 * max(1.0, np.abs(r).max()))
+        assert np.allclose(gb[sl].reshape(3, n), r, rtol=0, atol=1e-14 * max(1.0, np.abs(r).max(initial=0.0)))
 
 
 @pytest.mark.parametrize("precision", [lr.FP64, lr.MIXED])
