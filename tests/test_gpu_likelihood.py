@@ -263,7 +263,7 @@ def test_log_likelihood_autograd(ctx, flex, precision):
     xyz0 = host(plan.response(dev(hp), dev(hc), t0h, sky(src))).reshape(3, N)
     data = dev(oracle.aet(xyz0 + synth.white_noise(xyz0.shape, SIGMA, seed=4)))
     M = torch.tensor(aet_matrix(), device="cuda:0")
-    wt = torch.tensor(W, device="cuda:0")[:, None]
+    wt = torch.tensor(W, dtype=torch.float64, device="cuda:0")[:, None]
 
     def run(fn):
         a = dev(hp).requires_grad_()
@@ -271,7 +271,7 @@ def test_log_likelihood_autograd(ctx, flex, precision):
         s = torch.tensor(sky(src), dtype=torch.float64, device="cuda:0", requires_grad=True)
         L = fn(a, b, s)
         L.backward()
-        return float(L), host(a.grad), host(b.grad), host(s.grad)
+        return float(L.detach()), host(a.grad), host(b.grad), host(s.grad)
 
     L1, gp1, gc1, gs1 = run(lambda a, b, s: lr.log_likelihood(plan, a, b, s, t0h, data, W))
 
