@@ -202,3 +202,50 @@ def test_equal_arm_transfer_magnitude():
     amp0 = np.abs(np.fft.rfft(np.cos(omega * t[100:1900]) * np.hanning(1800))).max()
     expect = 4 * abs(np.sin(omega * L)) * abs(np.sin(2 * omega * L)) * abs(c[3] - c[0])
     assert abs(amp / amp0 - expect) < 1e-3 * expect
+
+
+@pytest.mark.parametrize("gen", [1, 2])
+@pytest.mark.parametrize("mode", ["summed", "nested"])
+def test_quadratic_links_reduce_tdi_to_its_chained_delays(gen, mode):
+    """With every link series the parabola y(t) = (t / 100 s)^2 (read exactly by the Lagrange FIR,
+    degree 2 <= p) and delays linear in time (reproduced exactly by the cubic spline), each delayed
+    term is y(t - D) for its chained delay D, so X follows by hand from Eqs. tdi1/tdi2: chain A of
+    X visits spacecraft 1 3 1 2 1 2 1 3 1 and chain B 1 2 1 3 1 3 1 2 1, X = A - B; a term's delay
+    adds L_ij for each hop i -> j before it; summed: every L at t; nested: each L at the time the
+    hop ends, t - (the delay so far).  Y, Z by the cyclic map.  (A ramp would not do for TDI-2: its
+    summed X2 vanishes identically.)"""
+    L0 = np.array([8.10, 8.25, 8.40, 8.20, 8.35, 8.05])
+    rate = np.array([2e-6, -3e-6, 1e-6, -1e-6, 4e-6, -2e-6])  # s per s: nested - summed ~ 1e-4 s
+    tk = synth.knot_grid(-2e6, 2e6, 1e5)
+    pos = np.repeat(synth.static_triangle(np.zeros(1))[:, :, :1], len(tk), axis=2)
+    delays = L0[:, None] + rate[:, None] * tk[None, :]
+    o = oracle.Orbit(tk, pos, delays)
+    N = 400
+    t = synth.sample_grid(T0, DT, N)
+    ys = lambda tt: (tt / 100.0) ** 2  # noqa: E731
+    y = np.repeat(ys(t)[None, :], 6, axis=0)
+    dm = oracle.DELAY_SUM if mode == "summed" else oracle.DELAY_NESTED
+    xyz = oracle.tdi(P, gen, DT, T0, N, o, y, dm)
+    Lf = lambda name, tt: L0[LINK_INDEX[name]] + rate[LINK_INDEX[name]] * tt  # noqa: E731
+    seqs = ([1, 3, 1, 2, 1, 2, 1, 3, 1], [1, 2, 1, 3, 1, 3, 1, 2, 1])
+    nterm = 4 if gen == 1 else 8
+    ref = np.zeros((3, N))
+    mag = np.zeros(N)
+    for ch in range(3):
+        cyc = lambda s: (s - 1 + ch) % 3 + 1  # noqa: E731
+        for c, sign in ((0, 1.0), (1, -1.0)):
+            seq = [cyc(s) for s in seqs[c]]
+            D = np.zeros(N)
+            ref[ch] += sign * ys(t)
+            mag += ys(t)
+            for q in range(1, nterm):
+                hop = f"{seq[q - 1]}{seq[q]}"
+                D = D + Lf(hop, t if mode == "summed" else t - D)
+                ref[ch] += sign * ys(t - D)
+                mag += ys(t - D)
+    sl = slice(60, N - 30)  # away from the zero-extended ends
+    tol = 1e-12 * mag[sl].max()
+    assert np.abs(xyz[:, sl] - ref[:, sl]).max() <= tol
+    if mode == "nested":  # the two forms really differ here
+        summed = oracle.tdi(P, gen, DT, T0, N, o, y, oracle.DELAY_SUM)
+        assert np.abs(summed[:, sl] - xyz[:, sl]).max() > 100 * tol
