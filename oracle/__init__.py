@@ -25,8 +25,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lr_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liblr_oracle.so")
+_SRC_Q = os.path.join(_HERE, "lr_oracle_quad.c")
+_LIB_Q = os.path.join(_BUILD, "liblr_oracle_quad.so")
 _lock = threading.Lock()
 _lib = None
+_libq = None
 
 NOT_A_KNOT = 0
 NATURAL = 1
@@ -35,14 +38,36 @@ DELAY_NESTED = 1
 
 
 def build(force: bool = False) -> str:
-    """Compile lr_oracle.c into oracle/_build/liblr_oracle.so (gcc, OpenMP)."""
+    """Compile lr_oracle.c into oracle/_build/liblr_oracle.so (gcc, OpenMP), and the same source
+    widened to binary128 (lr_oracle_quad.c) into liblr_oracle_quad.so."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
         cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
+    global _quad_error
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_Q))
+    if force or not os.path.exists(_LIB_Q) or os.path.getmtime(_LIB_Q) < newest:
+        tmp = _LIB_Q + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu11", "-fvisibility=hidden", "-o", tmp, _SRC_Q,
+               "-lm"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode == 0:
+            os.replace(tmp, _LIB_Q)
+            _quad_error = None
+        else:  # a toolchain without binary128 libm: only the binary128 checks are unavailable
+            _quad_error = r.stderr.strip()[-2000:]
     return _LIB
+
+
+_quad_error = None
+
+
+def quad_available() -> bool:
+    """True when the binary128 build of the oracle exists on this machine."""
+    build()
+    return os.path.exists(_LIB_Q) and _quad_error is None
 
 
 def _load():
@@ -83,6 +108,25 @@ def _load():
             fn.restype = res
             fn.argtypes = args
         _lib = lib
+        return lib
+
+
+def _load_quad():
+    global _libq
+    with _lock:
+        if _libq is not None:
+            return _libq
+    if not quad_available():
+        raise RuntimeError(f"the binary128 oracle could not be built: {_quad_error}")
+    with _lock:
+        lib = ctypes.CDLL(_LIB_Q)
+        D, I64, I, P = ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
+        common = [I, I, I, D, D, I64, P, I64, P, P, I, P, P, I64, D, D, D, D]
+        lib.orq_set_threads.restype, lib.orq_set_threads.argtypes = I, [I]
+        lib.orq_response.restype, lib.orq_response.argtypes = I, common + [P]
+        lib.orq_backward.restype, lib.orq_backward.argtypes = I, common + [P, P, P, P]
+        lib.orq_response_at.restype, lib.orq_response_at.argtypes = I, common + [P, I64, P]
+        _libq = lib
         return lib
 
 
@@ -218,6 +262,56 @@ def response_at(p, gen, dt, t0, n, porb, torb, hp, hc, t0h, lam, beta, psi, idx,
                                    idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(idx), _dp(xyz),
                                    1 if absval else 0), "response_at")
     return xyz
+
+
+def _quad_common(p, gen, dt, t0, n, t_knots, pos, delays, hp, hc, t0h, lam, beta, psi, delay_mode, bc):
+    tk, ps = _f64(t_knots), _f64(pos).reshape(9, -1)
+    dl = None if delays is None else _f64(delays).reshape(6, -1)
+    hp, hc = _f64(hp), _f64(hc)
+    keep = (tk, ps, dl, hp, hc)
+    args = [int(p), int(gen), int(delay_mode), float(dt), float(t0), int(n), tk.ctypes.data, len(tk), ps.ctypes.data,
+            None if dl is None else dl.ctypes.data, int(bc), hp.ctypes.data, hc.ctypes.data, len(hp), float(t0h),
+            float(lam), float(beta), float(psi)]
+    return args, keep
+
+
+def response_quad(p, gen, dt, t0, n, t_knots, pos, delays, hp, hc, t0h, lam, beta, psi,
+                  delay_mode: int = DELAY_SUM, bc: int = NOT_A_KNOT) -> np.ndarray:
+    """X, Y, Z of ``response`` (one orbit for projection and TDI, given by its knots) computed by
+    the same oracle source in binary128 and rounded once to FP64: the exact result of the
+    oracle's algorithm on these FP64 inputs, to ~2^-60 relative of the FP64 oracle's own error."""
+    args, keep = _quad_common(p, gen, dt, t0, n, t_knots, pos, delays, hp, hc, t0h, lam, beta, psi, delay_mode, bc)
+    xyz = np.empty((3, n))
+    _check(_load_quad().orq_response(*args, xyz.ctypes.data), "response_quad")
+    del keep
+    return xyz
+
+
+def response_at_quad(p, gen, dt, t0, n, t_knots, pos, delays, hp, hc, t0h, lam, beta, psi, idx,
+                     delay_mode: int = DELAY_SUM, bc: int = NOT_A_KNOT) -> np.ndarray:
+    """``response_at`` in binary128 (rounded once to FP64): sampled exact values of long series."""
+    args, keep = _quad_common(p, gen, dt, t0, n, t_knots, pos, delays, hp, hc, t0h, lam, beta, psi, delay_mode, bc)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    xyz = np.empty((3, len(idx)))
+    _check(_load_quad().orq_response_at(*args, idx.ctypes.data, len(idx), xyz.ctypes.data), "response_at_quad")
+    del keep
+    return xyz
+
+
+def backward_quad(p, gen, dt, t0, n, t_knots, pos, delays, hp, hc, t0h, lam, beta, psi, gxyz,
+                  delay_mode: int = DELAY_SUM, bc: int = NOT_A_KNOT):
+    """(g_h+, g_hx, g_sky) of ``backward`` computed in binary128 and rounded once to FP64."""
+    args, keep = _quad_common(p, gen, dt, t0, n, t_knots, pos, delays, hp, hc, t0h, lam, beta, psi, delay_mode, bc)
+    g = _f64(gxyz).reshape(3, n)
+    ghp, ghc, gs = np.empty(len(keep[3])), np.empty(len(keep[3])), np.empty(3)
+    _check(_load_quad().orq_backward(*args, g.ctypes.data, ghp.ctypes.data, ghc.ctypes.data, gs.ctypes.data),
+           "backward_quad")
+    del keep
+    return ghp, ghc, gs
+
+
+def set_threads_quad(n: int) -> int:
+    return int(_load_quad().orq_set_threads(int(n)))
 
 
 # ---------------------------------------------------------------- adjoints
