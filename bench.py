@@ -286,10 +286,10 @@ def run_ours(args):
     link_samples = 6.0 * job_samples
 
     # accuracy at the stated precision: sampled outputs of a few sources against the oracle
-    rel_err = err_ratio = None
+    parity = None
     if rank == 0 and not args.no_check:
-        rel_err, err_ratio = sampled_error(d_xyz, lens, srcs, out_off, orb, p,
-                                           1e-6 if precision == lr.MIXED else 1e-12)
+        parity = sampled_error(d_xyz, lens, srcs, out_off, orb, p, 1e-6 if precision == lr.MIXED else 1e-12,
+                               exact=precision == lr.FP64)
 
     # end to end through the host-buffer entry point: pinned host arrays in, X, Y, Z back in host
     # memory; the library pipelines chunks of sources (copy-in, kernel, copy-out overlapped).  The
@@ -358,8 +358,8 @@ def run_ours(args):
                              "unit": "TFLOP/s", "frac": FLOPS_PER_SAMPLE(p) * total_samples /
                              (statistics.mean(l64) * 1e-3) / 1e12 / FP64_NOMINAL_TFLOPS}}
         if rank == 0 and not args.no_check:
-            fp64["rel_error_vs_oracle"], fp64["error_over_bound"] = sampled_error(d_xyz, lens, srcs, out_off, orb,
-                                                                                  p, 1e-12)
+            fp64["parity"] = sampled_error(d_xyz, lens, srcs, out_off, orb, p, 1e-12, exact=True)
+            fp64["rel_error_vs_oracle"] = fp64["parity"]["rel_error_vs_oracle"]
 
     split = None
     if rank == 0 and not args.no_split:
@@ -393,7 +393,8 @@ def run_ours(args):
                        "precision": args.precision, "sources_per_gpu": args.sources,
                        "samples_per_gpu": total_samples, "l2": "inputs (%.1f GB) larger than L2" %
                        ((hp.nbytes + hc.nbytes) / 1e9), "tile": plan.desc.tile},
-            "rel_error_vs_oracle": rel_err, "error_over_bound": err_ratio, "roofline": roof, "e2e": e2e, "gpu_launches": (3 if precision == lr.MIXED else 2) * args.steps,
+            "rel_error_vs_oracle": parity and parity["rel_error_vs_oracle"],
+            "error_over_bound": parity and parity["error_over_bound"], "parity": parity, "roofline": roof, "e2e": e2e, "gpu_launches": (3 if precision == lr.MIXED else 2) * args.steps,
             "clocks": clocks, "fp64": fp64, "split": split, "likelihood": like}
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = oracle_rate(lens, srcs, p, orb)
@@ -440,16 +441,21 @@ def split_times(lr, ctx, p, dev, stream, reps=5):
     return out
 
 
-def sampled_error(d_xyz, lens, srcs, out_off, orb, p, tol, n_sources=6, n_idx=60):
-    """Over a few sources: the largest relative L2 error of sampled X, Y, Z against the oracle, and
-    the largest ratio of the error to its bound (the stated tolerance tol, or the rounding-error
-    scale K u ||E|| when that is larger: K = 2 (T + 16), u = 2^-53, E the response evaluated by the
-    oracle with |weights|, |coefficients| and |inputs|; low-frequency sources are ill-conditioned
-    by 1e4-1e7, so two FP64 programs cannot agree to 1e-12 there)."""
+def sampled_error(d_xyz, lens, srcs, out_off, orb, p, tol, n_sources=6, n_idx=60, exact=False):
+    """Over a few sources of the batch, sampled X, Y, Z against the FP64 oracle: the largest relative
+    L2 error, the largest ratio of the error to its bound (the stated tolerance tol, or the
+    rounding-error scale K u ||E|| when that is larger: K = 2 (T + 16), u = 2^-53, E the response
+    evaluated by the oracle with |weights|, |coefficients| and |inputs|; low-frequency sources are
+    ill-conditioned by 1e4-1e7, so two FP64 programs cannot agree to 1e-12 there) and how many
+    sources meet tol outright.  exact=True also compares with the exact value of the oracle's
+    algorithm (its binary128 build) and reports the FP64 oracle's own error beside it."""
     import oracle
     o = oracle.Orbit(orb.t_knots, orb.pos, None)
+    do_exact = exact and oracle.quad_available()
+    delays = o.delays_at_knots() if do_exact else None
     rng = np.random.default_rng(7)
-    worst, worst_ratio = 0.0, 0.0
+    worst, worst_ratio, meets, n = 0.0, 0.0, 0, 0
+    worst_exact = worst_oracle_exact = 0.0
     for s in rng.choice(len(lens), n_sources, replace=False):
         N = int(lens[s])
         idx = np.sort(rng.integers(0, N, n_idx))
@@ -460,10 +466,24 @@ def sampled_error(d_xyz, lens, srcs, out_off, orb, p, tol, n_sources=6, n_idx=60
         scale = oracle.response_at(*args, absval=True)
         got = d_xyz[3 * out_off[s]:3 * out_off[s + 1]].view(3, N)[:, idx].cpu().numpy()
         err = float(np.linalg.norm(got - ref))
-        bound = max(tol * np.linalg.norm(ref), 2 * (p + 17) * 2.0 ** -53 * np.linalg.norm(scale))
-        worst = max(worst, err / float(np.linalg.norm(ref)))
+        nref = float(np.linalg.norm(ref))
+        bound = max(tol * nref, 2 * (p + 17) * 2.0 ** -53 * np.linalg.norm(scale))
+        worst = max(worst, err / nref)
         worst_ratio = max(worst_ratio, err / bound)
-    return worst, worst_ratio
+        meets += err <= tol * nref
+        n += 1
+        if do_exact:
+            q = oracle.response_at_quad(p, 2, DT, T0, N, orb.t_knots, orb.pos, delays, hp, hc, t0h, src.lam,
+                                        src.beta, src.psi, idx)
+            nq = float(np.linalg.norm(q))
+            worst_exact = max(worst_exact, float(np.linalg.norm(got - q)) / nq)
+            worst_oracle_exact = max(worst_oracle_exact, float(np.linalg.norm(ref - q)) / nq)
+    out = {"rel_error_vs_oracle": worst, "error_over_bound": worst_ratio, "tol": tol, "sources_checked": n,
+           "sources_within_tol": int(meets), "outputs_per_source": n_idx}
+    if do_exact:
+        out["rel_error_vs_exact"] = worst_exact
+        out["oracle_fp64_rel_error_vs_exact"] = worst_oracle_exact
+    return out
 
 
 def main():

@@ -103,7 +103,9 @@ LR_API int lr_debug_fail_allocations(int after);
 
 /* ------------------------------------------------------------------ context */
 /* Binds the library to CUDA device `device` (>= 0).  *out is owned by the caller and freed
- * by lr_ctx_destroy. */
+ * by lr_ctx_destroy.  Also resolves the device addresses of the fixed arrays used by
+ * lr_response_batched_noalloc on this device (the CUDA runtime loads them here, not during that
+ * call). */
 LR_API int lr_ctx_create(int device, lr_ctx **out);
 LR_API int lr_ctx_destroy(lr_ctx *ctx);
 /* cudaError_t of the last failing CUDA call made through this context (0 if none). */
@@ -133,6 +135,16 @@ LR_API int lr_plan_destroy(lr_plan *plan);
 /* Input samples an output sample needs on each side of its own time: an input series that
  * covers [t0 - left*dt, t0 + (n-1)*dt + right*dt] gives every output a full stencil. */
 LR_API int lr_required_margin(const lr_plan *plan, int64_t *left, int64_t *right);
+/* Outputs of the plan's span [0, n) whose TDI reads all have full stencils inside that span
+ * (Eqs. tdi1/tdi2 with the reads of Sec. "Implementation"): every chained delay of output k,
+ * at most tdi_generation-dependent 3 or 7 link delays (the TDI orbit's bound), reads link
+ * samples floor(k - D/dt) - (p-1)/2 .. floor(k - D/dt) + (p+1)/2, so
+ *   *first = ceil(q * L_max / dt) + (p-1)/2 + 1,   *last = n - 2 - (p-1)/2.
+ * Outside [*first, *last] the zero extension of the link series before sample 0 and after
+ * sample n-1 enters the result; inside it the outputs equal those of a longer span, provided the
+ * strain covers lr_required_margin.  *first > *last means no output has full stencils.
+ * Errors: LR_ERR_INVALID_ARG for null pointers. */
+LR_API int lr_valid_range(const lr_plan *plan, int64_t *first, int64_t *last);
 /* Waits for `stream`, then reads and clears the plan's device error word: LR_OK, or
  * LR_ERR_DEVICE / LR_ERR_TIMEOUT if a kernel recorded a fault since the last check. */
 LR_API int lr_plan_check(lr_plan *plan, void *stream);
@@ -190,9 +202,12 @@ LR_API int lr_response_batched_host(lr_plan *plan, int64_t S, const int64_t *h_o
 /* ------------------------------------------------------------------ graphs and tuning */
 typedef struct lr_graph lr_graph;
 /* Captures one lr_response_batched call (batch-table kernels + persistent fused kernel) into an
- * instantiated CUDA graph.  The plan's batch workspace is reserved before the capture; the graph
- * keeps the given device pointers: rewrite the inputs in place between replays.  The batch
- * shape (S, offsets) must not change while the graph is used.  Owned by the caller. */
+ * instantiated CUDA graph.  The graph owns its batch tables (tile prefix sums and sky frames,
+ * allocated before the capture, freed by lr_graph_destroy), so later calls on the same plan, with
+ * any batch size, do not disturb it.  The graph keeps the given device pointers: rewrite the
+ * inputs in place between replays; the batch shape (S, offsets) must not change while the graph
+ * is used.  The plan (its error word and orbit tables) and the orbits must outlive the graph.
+ * Owned by the caller. */
 LR_API int lr_response_batched_graph(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
                                      const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
                                      double *xyz, lr_graph **out);
@@ -216,9 +231,9 @@ LR_API int lr_plan_autotune(lr_plan *plan, int64_t n_samples, int use_cache, voi
  *   frames, 88 * LR_NOALLOC_MAX_SOURCES bytes) are held by every GPU that loads the library until
  *   the process exits, and are shared by every call on that GPU: each call rewrites the entries
  *   it uses before reading them, and calls that overlap on the GPU (other streams, other threads,
- *   other plans) race on them.  The first call on a device looks up the arrays' device addresses
- *   (cudaGetSymbolAddress, with that device made current for the look-up); make that first call
- *   before any stream capture. */
+ *   other plans) race on them.  The arrays' device addresses are looked up (cudaGetSymbolAddress,
+ *   with that device current) by lr_ctx_create, which is also when the CUDA runtime loads the
+ *   module holding them, so this call itself allocates nothing. */
 #define LR_NOALLOC_MAX_SOURCES 65536
 LR_API int lr_response_batched_noalloc(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
                                        const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
@@ -251,6 +266,19 @@ LR_API int lr_likelihood_batched(lr_plan *plan, int64_t S, const int64_t *h_off,
                                  const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
                                  const double *data, int64_t n_total, const double *weights, double *dh_hh,
                                  double *xyz, void *stream);
+
+/* The log-likelihood of Eq. like up to the caller's constant -<d|d>/2, <d|h> - <h|h>/2, formed by
+ * the library from the same fused epilogue and per-source reduction as lr_likelihood: the only
+ * value that leaves the GPU per source (the paper's MCMC use, Sec. "Implementation").
+ *   logl : DEVICE double[1]; other arguments and errors as lr_likelihood. */
+LR_API int lr_log_likelihood(lr_plan *plan, const double *hp, const double *hc, int64_t n_h, double t0_h,
+                             lr_sky sky, const double *data, const double *weights, double *logl, double *xyz,
+                             void *stream);
+/* Batched form: logl is DEVICE double[S]; other arguments and errors as lr_likelihood_batched. */
+LR_API int lr_log_likelihood_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
+                                     const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
+                                     const double *data, int64_t n_total, const double *weights, double *logl,
+                                     double *xyz, void *stream);
 
 /* Gradient of the time-domain log-likelihood (up to the constant -<d|d>/2),
  * <d|h> - <h|h>/2 over A, E, T with the weights of lr_likelihood, with respect to the template's

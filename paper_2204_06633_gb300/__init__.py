@@ -74,6 +74,9 @@ _SIGS = {
     "lr_plan_autotune": (_I, [_P, _I64, _I, _P, ctypes.POINTER(_I)]),
     "lr_likelihood": (_I, [_P, _P, _P, _I64, _D, lr_sky, _P, _P, _P, _P, _P]),
     "lr_likelihood_batched": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _P, _P, _P]),
+    "lr_log_likelihood": (_I, [_P, _P, _P, _I64, _D, lr_sky, _P, _P, _P, _P, _P]),
+    "lr_log_likelihood_batched": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _P, _P, _P]),
+    "lr_valid_range": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "lr_likelihood_grad": (_I, [_P, _P, _P, _P, _D, _P, _P]),
     "lr_likelihood_grad_batched": (_I, [_P, _I64, _P, _I64, _P, _P, _P, _D, _P, _P]),
 }
@@ -236,6 +239,12 @@ class Plan:
         _check("lr_required_margin", library().lr_required_margin(self._h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
 
+    def valid_range(self):
+        """(first, last): the outputs whose TDI stencils lie inside [0, n) (inclusive bounds)."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check("lr_valid_range", library().lr_valid_range(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
     def check(self, stream=None):
         """Waits for the stream and raises if a kernel recorded a fault."""
         _check("lr_plan_check", library().lr_plan_check(self._h, _stream_handle(stream)))
@@ -296,6 +305,32 @@ class Plan:
             self._h, _dev64(hp, "hp"), _dev64(hc, "hc", hp.numel()), hp.numel(), float(t0h), _sky(sky),
             _dev64(data, "data", 3 * self.n), ctypes.addressof(w), _dev64(out, "dh_hh", 2),
             _dev64(xyz, "xyz", 3 * self.n) if xyz is not None else None, _stream_handle(stream)))
+        return out
+
+    def log_likelihood(self, hp, hc, t0h, sky, data, weights=(1.0, 1.0, 1.0), xyz=None, out=None, stream=None):
+        """<d|h> - <h|h>/2 as a float64 CUDA tensor [1], formed by the library (see likelihood)."""
+        out = self._out(out, (1,), hp)
+        w = (ctypes.c_double * 3)(*[float(x) for x in weights])
+        _check("lr_log_likelihood", library().lr_log_likelihood(
+            self._h, _dev64(hp, "hp"), _dev64(hc, "hc", hp.numel()), hp.numel(), float(t0h), _sky(sky),
+            _dev64(data, "data", 3 * self.n), ctypes.addressof(w), _dev64(out, "logl", 1),
+            _dev64(xyz, "xyz", 3 * self.n) if xyz is not None else None, _stream_handle(stream)))
+        return out
+
+    def log_likelihood_batched(self, h_off, out_off, t0h, sky, hp, hc, data, weights=(1.0, 1.0, 1.0), xyz=None,
+                               out=None, stream=None):
+        """Per-source <d|h> - <h|h>/2 as float64 CUDA [S] (arguments as likelihood_batched)."""
+        S = t0h.numel()
+        if data.numel() % 3:
+            raise ValueError("data must hold three channel blocks")
+        n_total = data.numel() // 3
+        out = self._out(out, (S,), hp)
+        w = (ctypes.c_double * 3)(*[float(x) for x in weights])
+        _check("lr_log_likelihood_batched", library().lr_log_likelihood_batched(
+            self._h, S, _devi64(h_off, "h_off", S + 1), _devi64(out_off, "out_off", S + 1), _dev64(t0h, "t0h", S),
+            _dev64(sky, "sky", 3 * S), _dev64(hp, "hp"), _dev64(hc, "hc", hp.numel()),
+            _dev64(data, "data", 3 * n_total), n_total, ctypes.addressof(w), _dev64(out, "logl", S),
+            _dev64(xyz, "xyz", 3 * n_total) if xyz is not None else None, _stream_handle(stream)))
         return out
 
     def likelihood_batched(self, h_off, out_off, t0h, sky, hp, hc, data, weights=(1.0, 1.0, 1.0), xyz=None,
@@ -429,7 +464,7 @@ class _Response(torch.autograd.Function):
     @staticmethod
     def forward(ctx, hp, hc, sky, plan, t0h):
         s = tuple(float(v) for v in sky.detach().cpu().tolist())
-        ctx.plan, ctx.t0h, ctx.sky = plan, t0h, s
+        ctx.plan, ctx.t0h, ctx.sky, ctx.sky_device = plan, t0h, s, sky.device
         ctx.save_for_backward(hp, hc)
         return plan.response(hp.contiguous(), hc.contiguous(), t0h, s)
 
@@ -438,7 +473,7 @@ class _Response(torch.autograd.Function):
         hp, hc = ctx.saved_tensors
         g_hp, g_hc, g_sky = ctx.plan.backward(hp.contiguous(), hc.contiguous(), ctx.t0h, ctx.sky,
                                               g_xyz.contiguous())
-        return g_hp, g_hc, g_sky.to(g_xyz.device), None, None
+        return g_hp, g_hc, g_sky.to(ctx.sky_device), None, None
 
 
 def response(plan: Plan, hp, hc, sky, t0h: float):
@@ -457,17 +492,17 @@ class _LogLikelihood(torch.autograd.Function):
     def forward(ctx, hp, hc, sky, plan, t0h, data, weights):
         s = tuple(float(v) for v in sky.detach().cpu().tolist())
         xyz = torch.empty((3, plan.n), dtype=torch.float64, device=hp.device)
-        dh_hh = plan.likelihood(hp.contiguous(), hc.contiguous(), t0h, s, data, weights, xyz=xyz)
-        ctx.plan, ctx.t0h, ctx.sky, ctx.weights = plan, t0h, s, weights
+        logl = plan.log_likelihood(hp.contiguous(), hc.contiguous(), t0h, s, data, weights, xyz=xyz)
+        ctx.plan, ctx.t0h, ctx.sky, ctx.weights, ctx.sky_device = plan, t0h, s, weights, sky.device
         ctx.save_for_backward(hp, hc, xyz, data)
-        return dh_hh[0] - 0.5 * dh_hh[1]
+        return logl[0]
 
     @staticmethod
     def backward(ctx, g):
         hp, hc, xyz, data = ctx.saved_tensors
         g_xyz = ctx.plan.likelihood_grad(xyz, data, ctx.weights, scale=float(g))
         g_hp, g_hc, g_sky = ctx.plan.backward(hp.contiguous(), hc.contiguous(), ctx.t0h, ctx.sky, g_xyz)
-        return g_hp, g_hc, g_sky.to(hp.device), None, None, None, None
+        return g_hp, g_hc, g_sky.to(ctx.sky_device), None, None, None, None
 
 
 def log_likelihood(plan: Plan, hp, hc, sky, t0h: float, data, weights=(1.0, 1.0, 1.0)):

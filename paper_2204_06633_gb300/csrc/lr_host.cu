@@ -317,6 +317,13 @@ LR_API int lr_ctx_create(int device, lr_ctx **out)
         delete c;
         return LR_ERR_CUDA;
     }
+    // the fixed arrays of lr_response_batched_noalloc are resolved (and their module loaded) here
+    const int ne = lr::noalloc_setup(device);
+    if (ne) {
+        c->last_cuda_error = ne;
+        delete c;
+        return ne == (int)cudaErrorMemoryAllocation ? LR_ERR_OOM : LR_ERR_CUDA;
+    }
     *out = c;
     return LR_OK;
 }
@@ -576,6 +583,17 @@ LR_API int lr_required_margin(const lr_plan *plan, int64_t *left, int64_t *right
     return LR_OK;
 }
 
+LR_API int lr_valid_range(const lr_plan *plan, int64_t *first, int64_t *last)
+{
+    if (!plan || !first || !last) return LR_ERR_INVALID_ARG;
+    // the chained delays reach back by at most q_terms link delays; a read at fractional
+    // position x uses samples floor(x) - h .. floor(x) + h + 1
+    const double chain = (double)plan->base.q_terms * plan->desc.tdi_orbit->max_delay / plan->desc.dt;
+    *first = (int64_t)std::ceil(chain) + plan->h + 1;
+    *last = plan->desc.n - 2 - plan->h;
+    return LR_OK;
+}
+
 LR_API int lr_plan_check(lr_plan *plan, void *stream)
 {
     if (!plan) return LR_ERR_INVALID_ARG;
@@ -783,8 +801,13 @@ double like_post(const lr_plan *plan, const lr::FwdParams &P)
 
 extern "C" {
 
-LR_API int lr_likelihood(lr_plan *plan, const double *hp, const double *hc, int64_t n_h, double t0_h, lr_sky sky,
-                         const double *data, const double *weights, double *dh_hh, double *xyz, void *stream)
+}  // extern "C"
+
+namespace {
+
+// the fused likelihood launch and its per-source reduction; logl selects the output form
+int likelihood_single(lr_plan *plan, const double *hp, const double *hc, int64_t n_h, double t0_h, lr_sky sky,
+                      const double *data, const double *weights, int logl, double *dh_hh, double *xyz, void *stream)
 {
     if (!plan || !hp || !hc || !data || !weights || !dh_hh) return LR_ERR_INVALID_ARG;
     if (n_h < 1) return LR_ERR_INVALID_ARG;
@@ -806,13 +829,12 @@ LR_API int lr_likelihood(lr_plan *plan, const double *hp, const double *hc, int6
     st = launch_single(plan, lr::KIND_LIKE, P, stream);
     if (st) return st;
     return check_launch(plan->ctx, lr::launch_like_reduce(plan->d_lpart, nullptr, tiles, 1, plan->lpart_cap,
-                                                          like_post(plan, P), dh_hh, plan->d_err, stream));
+                                                          like_post(plan, P), logl, dh_hh, plan->d_err, stream));
 }
 
-LR_API int lr_likelihood_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
-                                 const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
-                                 const double *data, int64_t n_total, const double *weights, double *dh_hh,
-                                 double *xyz, void *stream)
+int likelihood_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off, const double *t0_h,
+                       const lr_sky *sky, const double *hp, const double *hc, const double *data, int64_t n_total,
+                       const double *weights, int logl, double *dh_hh, double *xyz, void *stream)
 {
     if (!plan || !h_off || !out_off || !t0_h || !sky || !hp || !hc || !data || !weights || !dh_hh)
         return LR_ERR_INVALID_ARG;
@@ -842,7 +864,42 @@ LR_API int lr_likelihood_batched(lr_plan *plan, int64_t S, const int64_t *h_off,
                                                     plan->threads, plan->ctx->sms, stream));
     if (st) return st;
     return check_launch(plan->ctx, lr::launch_like_reduce(plan->d_lpart, plan->d_tile_off, 0, S, plan->lpart_cap,
-                                                          like_post(plan, P), dh_hh, plan->d_err, stream));
+                                                          like_post(plan, P), logl, dh_hh, plan->d_err, stream));
+}
+
+}  // namespace
+
+extern "C" {
+
+LR_API int lr_likelihood(lr_plan *plan, const double *hp, const double *hc, int64_t n_h, double t0_h, lr_sky sky,
+                         const double *data, const double *weights, double *dh_hh, double *xyz, void *stream)
+{
+    return likelihood_single(plan, hp, hc, n_h, t0_h, sky, data, weights, 0, dh_hh, xyz, stream);
+}
+
+LR_API int lr_likelihood_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
+                                 const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
+                                 const double *data, int64_t n_total, const double *weights, double *dh_hh,
+                                 double *xyz, void *stream)
+{
+    return likelihood_batched(plan, S, h_off, out_off, t0_h, sky, hp, hc, data, n_total, weights, 0, dh_hh, xyz,
+                              stream);
+}
+
+LR_API int lr_log_likelihood(lr_plan *plan, const double *hp, const double *hc, int64_t n_h, double t0_h,
+                             lr_sky sky, const double *data, const double *weights, double *logl, double *xyz,
+                             void *stream)
+{
+    return likelihood_single(plan, hp, hc, n_h, t0_h, sky, data, weights, 1, logl, xyz, stream);
+}
+
+LR_API int lr_log_likelihood_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
+                                     const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
+                                     const double *data, int64_t n_total, const double *weights, double *logl,
+                                     double *xyz, void *stream)
+{
+    return likelihood_batched(plan, S, h_off, out_off, t0_h, sky, hp, hc, data, n_total, weights, 1, logl, xyz,
+                              stream);
 }
 
 LR_API int lr_likelihood_grad(lr_plan *plan, const double *xyz, const double *data, const double *weights,

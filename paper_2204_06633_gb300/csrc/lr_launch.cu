@@ -95,10 +95,11 @@ int launch_batch_tables(const int64_t *out_off, const lr_sky *sky, int64_t S, in
 // (lane l takes tiles l, l + 32, ... in order, then a fixed shuffle tree), so the result does not
 // depend on the launch or on timing; the sums are multiplied by post (the weight normalisation
 // of the mixed epilogue, 1 otherwise).  tile_off == nullptr: one source of tiles1 tiles.
+// logl != 0: out[s] = (<d|h> - <h|h>/2) * post instead of the pair.
 __global__ void __launch_bounds__(256) k_like_reduce(const double *__restrict__ partial,
                                                      const int64_t *__restrict__ tile_off, int64_t tiles1,
-                                                     int64_t S, int64_t cap, double post, double *__restrict__ out,
-                                                     int *err)
+                                                     int64_t S, int64_t cap, double post, int logl,
+                                                     double *__restrict__ out, int *err)
 {
     const int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -107,7 +108,9 @@ __global__ void __launch_bounds__(256) k_like_reduce(const double *__restrict__ 
     if (a < 0 || b < a || b > cap) {
         if (lane == 0) {
             atomicOr(err, ERR_OFFSETS);
-            out[2 * s] = out[2 * s + 1] = __longlong_as_double(0x7ff8000000000000ll);
+            const double nan = __longlong_as_double(0x7ff8000000000000ll);
+            if (logl) out[s] = nan;
+            else out[2 * s] = out[2 * s + 1] = nan;
         }
         return;
     }
@@ -121,8 +124,12 @@ __global__ void __launch_bounds__(256) k_like_reduce(const double *__restrict__ 
         hh += __shfl_down_sync(0xffffffffu, hh, o);
     }
     if (lane == 0) {
-        out[2 * s] = dh * post;
-        out[2 * s + 1] = hh * post;
+        if (logl) {
+            out[s] = fma(-0.5, hh, dh) * post;
+        } else {
+            out[2 * s] = dh * post;
+            out[2 * s + 1] = hh * post;
+        }
     }
 }
 
@@ -169,11 +176,11 @@ int launch_like_grad(const int64_t *out_off, int64_t S, int64_t n1, const double
 }
 
 int launch_like_reduce(const double *partial, const int64_t *tile_off, int64_t tiles1, int64_t S, int64_t cap,
-                       double post, double *out, int *err, void *stream)
+                       double post, int logl, double *out, int *err, void *stream)
 {
     const int64_t blocks = (S + 7) / 8;
-    k_like_reduce<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(partial, tile_off, tiles1, S, cap, post, out,
-                                                                     err);
+    k_like_reduce<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(partial, tile_off, tiles1, S, cap, post, logl,
+                                                                     out, err);
     return (int)cudaGetLastError();
 }
 

@@ -17,7 +17,8 @@ bool order_compiled(int order);
 // block (out_off == nullptr: one source of n1)
 int launch_like_grad(const int64_t *out_off, int64_t S, int64_t n1, const double *x, const double *d,
                      const double *w, double scale, double *g, int *err, void *stream);
-// per-source (<d|h>, <h|h>) from the per-tile partials of a likelihood launch, times post
+// per-source (<d|h>, <h|h>) from the per-tile partials of a likelihood launch, times post; with
+// logl != 0 one value per source instead, <d|h> - <h|h>/2
 int launch_like_reduce(const double *partial, const int64_t *tile_off, int64_t tiles1, int64_t S, int64_t cap,
-                       double post, double *out, int *err, void *stream);
+                       double post, int logl, double *out, int *err, void *stream);
 }  // namespace lr

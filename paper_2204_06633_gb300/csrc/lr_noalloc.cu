@@ -62,6 +62,18 @@ int table_address(int device, int64_t **out, lr::SkyConst **sky_out)
 
 }  // namespace
 
+namespace lr {
+// Called by lr_ctx_create with `device` current: looks up the arrays' device addresses now, which
+// also makes the CUDA runtime load this file's module (and allocate the arrays) during set-up
+// rather than inside a caller's first allocation-free call.
+int noalloc_setup(int device)
+{
+    int64_t *table = nullptr;
+    SkyConst *sky = nullptr;
+    return table_address(device, &table, &sky);
+}
+}  // namespace lr
+
 extern "C" LR_API int lr_response_batched_noalloc(lr_plan *plan, int64_t S, const int64_t *h_off,
                                                   const int64_t *out_off, const double *t0_h, const lr_sky *sky,
                                                   const double *hp, const double *hc, double *xyz, void *stream)

@@ -23,5 +23,8 @@ SkyConst *plan_sky_table(lr_plan *plan);
 cudaError_t dev_malloc(void **p, size_t bytes);
 // records a failing cudaError_t in the plan's context and returns LR_ERR_CUDA
 int plan_cuda_fail(lr_plan *plan, int cuda_error);
+// looks up the allocation-free entry point's fixed device arrays on `device` (current); returns a
+// cudaError_t value
+int noalloc_setup(int device);
 
 }  // namespace lr

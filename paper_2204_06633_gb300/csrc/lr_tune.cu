@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -24,6 +25,10 @@
 struct lr_graph {
     cudaGraph_t graph;
     cudaGraphExec_t exec;
+    // the graph's own batch tables (tile prefix sums [S+1], then the sources' sky frames [S+1]):
+    // the plan's batch tables are re-allocated when a later call brings a larger batch, so a
+    // replay must not depend on them
+    int64_t *tables;
 };
 
 namespace {
@@ -86,27 +91,52 @@ LR_API int lr_response_batched_graph(lr_plan *plan, int64_t S, const int64_t *h_
     *out = nullptr;
     if (S < 1) return LR_ERR_INVALID_ARG;
     if (S > (int64_t)1 << 24) return LR_ERR_RANGE;
-    int st = lr::plan_reserve_batch(plan, S);  // nothing may allocate during the capture
+    if (!h_off || !out_off || !t0_h || !sky || !hp || !hc || !xyz) return LR_ERR_INVALID_ARG;
+    lr::PlanView v;
+    int st = lr::plan_view(plan, &v);
     if (st) return st;
-    cudaStream_t cs;
-    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return lr::plan_cuda_fail(plan, e);
-    lr_graph *g = new lr_graph();
+    lr_graph *g = new (std::nothrow) lr_graph();
+    if (!g) return LR_ERR_OOM;
     g->graph = nullptr;
     g->exec = nullptr;
-    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-        st = lr_response_batched(plan, S, h_off, out_off, t0_h, sky, hp, hc, xyz, cs);
-        cudaError_t e2 = cudaStreamEndCapture(cs, &g->graph);
-        if (st == LR_OK && e2 != cudaSuccess) e = e2;
+    g->tables = nullptr;
+    // the graph's tables are allocated before the capture (nothing may allocate during it)
+    cudaError_t e = lr::dev_malloc((void **)&g->tables, (sizeof(int64_t) + sizeof(lr::SkyConst)) * (size_t)(S + 1));
+    if (e != cudaSuccess) {
+        delete g;
+        return e == cudaErrorMemoryAllocation ? LR_ERR_OOM : lr::plan_cuda_fail(plan, e);
     }
-    if (e == cudaSuccess && st == LR_OK) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
-    cudaStreamDestroy(cs);
-    if (st != LR_OK || e != cudaSuccess) {
+    lr::SkyConst *skyc =
+        v.precision == LR_MIXED ? reinterpret_cast<lr::SkyConst *>(g->tables + (S + 1)) : nullptr;
+    cudaStream_t cs = nullptr;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        lr::FwdParams P = v.base;
+        int le = lr::launch_batch_tables(out_off, sky, S, P.tile, g->tables, skyc, P.err, cs);
+        P.src.skyc = skyc;
+        P.src.h_off = h_off;
+        P.src.out_off = out_off;
+        P.src.t0h = t0_h;
+        P.src.sky = sky;
+        P.src.tile_off = g->tables;
+        P.src.S = S;
+        P.hp = hp;
+        P.hc = hc;
+        P.out = xyz;
+        P.total_tiles = -1;
+        if (!le) le = lr::launch_forward(v.precision, lr::KIND_FUSED, v.order, P, v.threads, v.sms, cs);
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g->graph);
+        e = le ? (cudaError_t)le : e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
         if (g->exec) cudaGraphExecDestroy(g->exec);
         if (g->graph) cudaGraphDestroy(g->graph);
+        cudaFree(g->tables);
         delete g;
-        return st != LR_OK ? st : lr::plan_cuda_fail(plan, e);
+        return lr::plan_cuda_fail(plan, e);
     }
     *out = g;
     return LR_OK;
@@ -123,6 +153,7 @@ LR_API int lr_graph_destroy(lr_graph *graph)
     if (!graph) return LR_ERR_INVALID_ARG;
     if (graph->exec) cudaGraphExecDestroy(graph->exec);
     if (graph->graph) cudaGraphDestroy(graph->graph);
+    if (graph->tables) cudaFree(graph->tables);
     delete graph;
     return LR_OK;
 }

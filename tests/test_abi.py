@@ -54,6 +54,10 @@ def test_null_arguments_are_rejected_on_the_host(lib):
     assert lib.lr_plan_create(None, None, None) == 1
     assert lib.lr_orbit_destroy(None) == 1
     assert lib.lr_required_margin(None, None, None) == 1
+    assert lib.lr_valid_range(None, None, None) == 1
+    assert lib.lr_log_likelihood(None, None, None, 0, 0.0, lr.lr_sky(), None, None, None, None, None) == 1
+    assert lib.lr_log_likelihood_batched(None, 1, None, None, None, None, None, None, None, 0, None, None, None,
+                                         None) == 1
     assert lib.lr_likelihood(None, None, None, 0, 0.0, lr.lr_sky(), None, None, None, None, None) == 1
     assert lib.lr_likelihood_batched(None, 1, None, None, None, None, None, None, None, 0, None, None, None,
                                      None) == 1

@@ -83,3 +83,22 @@ def test_autotune_picks_a_candidate_and_keeps_results(setup, precision, rel, tmp
     assert f"|o{P}|" in text and f" {tile} " in text
     again = lr.Plan(ctx, P, N, DT, o, t0=T0, precision=precision)
     assert again.autotune(N, use_cache=True) == tile
+
+
+@pytest.mark.parametrize("precision", [lr.FP64, lr.MIXED])
+def test_graph_survives_a_larger_batch_on_the_same_plan(setup, precision):
+    """A larger batched call on the plan after the capture re-allocates the plan's batch tables;
+    the graph keeps its own and still replays its batch."""
+    ctx, o = setup
+    plan = lr.Plan(ctx, P, 1, DT, o, t0=T0, precision=precision)
+    lens = [2500, 700]
+    args = make_batch(lens, 43)
+    xyz = torch.zeros(3 * sum(lens), dtype=torch.float64, device="cuda:0")
+    g = plan.response_batched_graph(*args, xyz)
+    big = make_batch([300] * 64, 44)
+    plan.response_batched(*big)          # grows (re-allocates) the plan's batch tables
+    g.launch()
+    torch.cuda.synchronize()
+    ref = plan.response_batched(*args)
+    plan.check()
+    assert torch.equal(xyz, ref)

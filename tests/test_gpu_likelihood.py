@@ -313,3 +313,32 @@ def test_likelihood_grad_batched_refuses_offsets_past_the_arrays(ctx, flex):
     assert torch.all(g[2100:] == 7.0)  # the second source is not touched ...
     with pytest.raises(lr.LRError):    # ... and the error word says why
         plan.check()
+
+
+@pytest.mark.parametrize("precision", [lr.FP64, lr.MIXED])
+def test_log_likelihood_entry_points_match_the_pair(ctx, flex, precision):
+    """lr_log_likelihood(_batched) returns <d|h> - <h|h>/2 from the same per-tile partials as
+    lr_likelihood(_batched): equal up to the one rounding of forming the difference."""
+    p = 11
+    lens = [5000, 0, 1, 3001]
+    srcs, h_off, out_off, t0h, sky_, hp, hc = batch(lens, 51, p)
+    data = np.random.default_rng(2).normal(size=3 * int(out_off[-1])) * SIGMA
+    plan = lr.Plan(ctx, p, 1, DT, flex.gpu, t0=T0, precision=precision)
+    d = lambda a: torch.tensor(a, device="cuda:0")  # noqa: E731
+    dargs = (d(h_off), d(out_off), d(t0h), d(sky_), d(hp), d(hc), d(data))
+    pair = host(plan.likelihood_batched(*dargs, weights=W))
+    logl = host(plan.log_likelihood_batched(*dargs, weights=W))
+    plan.check()
+    assert logl.shape == (len(lens),)
+    ref = pair[:, 0] - 0.5 * pair[:, 1]
+    tol = 4 * 2.0 ** -53 * (np.abs(pair[:, 0]) + np.abs(pair[:, 1]))
+    assert np.all(np.abs(logl - ref) <= tol)
+    # single source
+    N = lens[0]
+    plan1 = lr.Plan(ctx, p, N, DT, flex.gpu, t0=T0, precision=precision)
+    hs = slice(h_off[0], h_off[1])
+    sd = dev(data[:3 * N])
+    pr = host(plan1.likelihood(dev(hp[hs]), dev(hc[hs]), t0h[0], sky_[0], sd, W))
+    l1 = host(plan1.log_likelihood(dev(hp[hs]), dev(hc[hs]), t0h[0], sky_[0], sd, W))
+    plan1.check()
+    assert abs(l1[0] - (pr[0] - 0.5 * pr[1])) <= 4 * 2.0 ** -53 * (abs(pr[0]) + abs(pr[1]))

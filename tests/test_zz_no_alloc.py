@@ -1,8 +1,9 @@
 """lr_response_batched_noalloc: the batched forward for callers that may not allocate device
 memory once their run has started (its tile table lives in a fixed device array inside the
 library).  Its X, Y, Z must equal those of lr_response_batched, call after call, although the
-shared array keeps the previous call's contents; batches beyond the array's capacity are
-refused before anything runs.  Kept in a file collected last so that a failure here leaves
+shared array keeps the previous call's contents; the calls run with every library allocation
+made to fail and leave the device's free memory unchanged; batches beyond the array's capacity
+are refused before anything runs.  Kept in a file collected last so that a failure here leaves
 every other test already run."""
 import numpy as np
 import pytest
@@ -54,10 +55,21 @@ def test_noalloc_matches_batched_on_consecutive_calls(precision, rel):
     plan = lr.Plan(ctx, P, 1, DT, o, t0=T0, precision=precision)
     # a larger batch first, then a smaller one: the second call runs on top of the table
     # contents the first one left behind
+    lib = lr.library()
     for lens, seed in (([777, 5000, 0, 12345, 300, 65536], 31), ([4096, 1, 2000], 32)):
         args, out_off = batch(lens, seed)
         ref = plan.response_batched(*args)
-        got = plan.response_batched_noalloc(*args, xyz=torch.full_like(ref, float("nan")))
+        out = torch.full_like(ref, float("nan"))
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
+        # every library allocation fails while this is armed: the call must not need one
+        lib.lr_debug_fail_allocations(0)
+        try:
+            got = plan.response_batched_noalloc(*args, xyz=out)
+            torch.cuda.synchronize()
+        finally:
+            lib.lr_debug_fail_allocations(-1)
+        assert torch.cuda.mem_get_info()[0] == free_before  # and no allocation outside the library
         plan.check()
         assert torch.isfinite(got).all()
         assert per_source_rel(got, ref, out_off) <= rel
