@@ -45,11 +45,20 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 MIXED_P25_DRAM_BYTES_PER_SAMPLE = 236_457_472 / 7_115_014
 
 
-def workload(rank: int, n_sources: int):
-    seed = 3 + 1000 * rank
-    lens = synth.ragged_lengths(n_sources, seed=seed)
-    srcs = synth.draw_sources(n_sources, seed=seed + 1, A=1e-22, fdot=1e-17)
-    return lens, srcs
+def workload(rank: int, world: int, n_sources: int):
+    """This rank's share of the job's batch: world * n_sources sources (N_s ~ U[2^16, 2^20], seed 3;
+    parameters seed 4) dealt over the ranks by the library's length-balanced partition
+    (lr_partition_sources), so the work per GPU stays fixed as ranks are added (weak scaling) and
+    one rank runs exactly the 1024-source batch."""
+    total = world * n_sources
+    lens = synth.ragged_lengths(total, seed=3)
+    srcs = synth.draw_sources(total, seed=4, A=1e-22, fdot=1e-17)
+    if world == 1:
+        return lens, srcs
+    import paper_2204_06633_gb300 as lr
+    rank_of, _ = lr.partition_sources(lens, world)
+    sel = np.flatnonzero(rank_of == rank)
+    return lens[sel], [srcs[i] for i in sel]
 
 
 def build_inputs(lens, srcs, p):
@@ -192,7 +201,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    lens, srcs = workload(0, S_SOURCES)
+    lens, srcs = workload(0, 1, S_SOURCES)
     orb = synth.orbit_flexing(T0 - 3e5, T0 + DT * int(lens.max()) + 3e5)
     times = []
     cb = None
@@ -224,7 +233,7 @@ def run_ours(args):
     import paper_2204_06633_gb300 as lr
 
     p = args.order
-    lens, srcs = workload(rank, args.sources)
+    lens, srcs = workload(rank, ws, args.sources)
     total_samples = int(lens.sum())
     orb = synth.orbit_flexing(T0 - 3e5, T0 + DT * int(lens.max()) + 3e5)
     h_off, out_off, t0h, sky, hp, hc = build_inputs(lens, srcs, p)
@@ -281,6 +290,10 @@ def run_ours(args):
 
     precision = lr.MIXED if args.precision == "mixed" else lr.FP64
     plan = lr.Plan(ctx, p, 1, DT, o, t0=T0, precision=precision, tile=args.tile)
+    tile_source = "given"
+    if not args.tile:  # the tile the batch autotuner picks for this batch's length mix
+        plan.autotune_batch(lens, use_cache=False, stream=stream)
+        tile_source = "lr_plan_autotune_batch on this batch"
     ms_step, launch_ms, clocks, step = timed(plan, args.steps, args.warmup, sample_clocks=True)
     value, ms_step, job_samples = job_throughput(total_samples, ms_step, dev)
     link_samples = 6.0 * job_samples
@@ -350,8 +363,10 @@ def run_ours(args):
     fp64 = None
     if precision == lr.MIXED and not args.no_fp64:
         plan64 = lr.Plan(ctx, p, 1, DT, o, t0=T0, precision=lr.FP64)
+        plan64.autotune_batch(lens, use_cache=False, stream=stream)
         ms64, l64, _, _ = timed(plan64, 2, 1)
         fp64 = {"value": link_samples / (ms64 * 1e-3), "unit": "link-samples/s", "ms_per_step": ms64,
+                "tile": plan64.tile,
                 "steps": 2, "warmup": 1, "mixed_speedup": ms64 / ms_step,
                 "roofline": {"bound": "alu", "achieved": FLOPS_PER_SAMPLE(p) * total_samples /
                              (statistics.mean(l64) * 1e-3) / 1e12, "peak": FP64_NOMINAL_TFLOPS,
@@ -375,7 +390,7 @@ def run_ours(args):
         peak_tflops, src_peak = FP32_PEAK_TFLOPS, ("FP32 ALU peak 152 SM x 128 lanes x 2 flop x 2.07 GHz "
                                                    "(own FFMA probe: 74.9 TFLOP/s)")
     traffic = None
-    if precision == lr.MIXED and p == 25 and not args.tile:
+    if precision == lr.MIXED and p == 25 and plan.tile == 340:
         traffic = MIXED_P25_DRAM_BYTES_PER_SAMPLE * total_samples
     roof = {"bound": "alu", "achieved": flops / avg_launch_s / 1e12, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": flops / avg_launch_s / 1e12 / peak_tflops, "traffic": traffic, "peak_source": src_peak,
@@ -392,52 +407,124 @@ def run_ours(args):
                                    "one persistent launch per step" % (total_samples, p),
                        "precision": args.precision, "sources_per_gpu": args.sources,
                        "samples_per_gpu": total_samples, "l2": "inputs (%.1f GB) larger than L2" %
-                       ((hp.nbytes + hc.nbytes) / 1e9), "tile": plan.desc.tile},
+                       ((hp.nbytes + hc.nbytes) / 1e9), "tile": plan.tile, "tile_source": tile_source},
             "rel_error_vs_oracle": parity and parity["rel_error_vs_oracle"],
             "error_over_bound": parity and parity["error_over_bound"], "parity": parity, "roofline": roof, "e2e": e2e, "gpu_launches": (3 if precision == lr.MIXED else 2) * args.steps,
             "clocks": clocks, "fp64": fp64, "split": split, "likelihood": like}
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = oracle_rate(lens, srcs, p, orb)
+        if args.oracle_configs:
+            line["cpu_baseline"]["configs_in_full"] = oracle_configs(p)
     print(json.dumps(line), flush=True)
+
+
+def _time_call(f, stream, reps=5):
+    """median of `reps` CUDA-event timings of f() on `stream` after 3 warm-up calls (ms)"""
+    import torch
+    for _ in range(3):
+        f()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        f()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
 
 
 def split_times(lr, ctx, p, dev, stream, reps=5):
     """The paper's split on its own workload: one one-year source (N = 3,153,600 at dt = 10 s),
     projection alone (h -> six links), TDI-2 alone (links -> X, Y, Z) and the fused call, in each
-    precision; CUDA events on the launching stream, median of `reps` after 3 warm-up calls."""
+    precision; the fused call for Lagrange orders 11 / 25 / 41 (the paper's order experiment); and
+    the templates: generic (flexing orbit), equal-arm (constant equal arms: the TDI delays are plan
+    constants, which the FP64 kernels read with fixed weights), equal-arm with light-time delays
+    (the same constellation on the time-dependent-delay path) and hybrid (flexing orbit for the
+    projection, constant equal arms for TDI).  CUDA events on the launching stream, median of
+    `reps` after 3 warm-up calls."""
     import torch
 
     N = 3_153_600
-    orb = synth.orbit_flexing(T0 - 3e5, T0 + DT * N + 3e5)
+    span = (T0 - 3e5, T0 + DT * N + 3e5)
+    orb = synth.orbit_flexing(*span)
     o = lr.Orbit(ctx, orb.t_knots, orb.pos, None)
     src = synth.draw_sources(1, seed=1, A=1e-21, fdot=1e-17)[0]
-    t0h, hp, hc = synth.gb_input(src, T0, DT, N, p)
-    d_hp = torch.tensor(hp, device=dev)
-    d_hc = torch.tensor(hc, device=dev)
     sky = (src.lam, src.beta, src.psi)
     y = torch.empty(6 * N, dtype=torch.float64, device=dev)
     xyz = torch.empty(3 * N, dtype=torch.float64, device=dev)
     out = {"workload": "one source, N = 3,153,600 (one year at dt 10 s), flexing orbit, order %d" % p}
+    inputs = {}
+
+    def strain(order):
+        if order not in inputs:
+            t0h, hp, hc = synth.gb_input(src, T0, DT, N, order)
+            inputs[order] = (t0h, torch.tensor(hp, device=dev), torch.tensor(hc, device=dev))
+        return inputs[order]
+
     for name, prec in (("mixed", lr.MIXED), ("fp64", lr.FP64)):
+        t0h, d_hp, d_hc = strain(p)
         plan = lr.Plan(ctx, p, N, DT, o, t0=T0, precision=prec)
         calls = {"project": lambda: plan.project(d_hp, d_hc, t0h, sky, y, stream=stream),
                  "tdi": lambda: plan.tdi(y, xyz, stream=stream),
                  "fused": lambda: plan.response(d_hp, d_hc, t0h, sky, xyz, stream=stream)}
-        res = {}
-        for k, f in calls.items():
-            for _ in range(3):
-                f()
-            ts = []
-            for _ in range(reps):
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                f()
-                b.record(stream)
-                b.synchronize()
-                ts.append(a.elapsed_time(b))
-            res[k + "_ms"] = statistics.median(ts)
+        out[name] = {k + "_ms": _time_call(f, stream, reps) for k, f in calls.items()}
         plan.check(stream)
-        out[name] = res
+    out["orders_fused_ms"] = {}
+    for order in (11, 25, 41):
+        t0h, d_hp, d_hc = strain(order)
+        res = {}
+        for name, prec in (("mixed", lr.MIXED), ("fp64", lr.FP64)):
+            plan = lr.Plan(ctx, order, N, DT, o, t0=T0, precision=prec)
+            res[name] = _time_call(lambda: plan.response(d_hp, d_hc, t0h, sky, xyz, stream=stream), stream, reps)
+            plan.check(stream)
+        out["orders_fused_ms"][str(order)] = res
+    eq = synth.orbit_equal_arm(*span, constant_arms=True)
+    eq_o = lr.Orbit(ctx, eq.t_knots, eq.pos, eq.delays)
+    eq_lt = lr.Orbit(ctx, eq.t_knots, eq.pos, None)
+    templates = {"generic": (o, o), "equal_arm": (eq_o, eq_o), "equal_arm_lighttime": (eq_lt, eq_lt),
+                 "hybrid": (o, eq_o)}
+    out["templates_fused_ms"] = {}
+    t0h, d_hp, d_hc = strain(p)
+    for tname, (po, to) in templates.items():
+        res = {}
+        for name, prec in (("mixed", lr.MIXED), ("fp64", lr.FP64)):
+            plan = lr.Plan(ctx, p, N, DT, po, to, t0=T0, precision=prec)
+            res[name] = _time_call(lambda: plan.response(d_hp, d_hc, t0h, sky, xyz, stream=stream), stream, reps)
+            plan.check(stream)
+        out["templates_fused_ms"][tname] = res
+    return out
+
+
+def oracle_configs(p=25):
+    """The FP64 oracle (as it stands, all host cores) on the small configurations in full:
+    config 1 (static triangle, N = 65,536, order 25, forward), config 2 (one flexing-orbit one-year
+    source, N = 3,153,600, forward) and config 4 (config 1's source at N = 65,536, forward + adjoint
+    against white-noise residuals); seconds and link-samples/s."""
+    import oracle
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    out = {"cores": cores}
+    src1 = synth.config1_source()
+    for name, N, orbf, src in (("config1", 65536, synth.orbit_static, src1),
+                               ("config2", 3_153_600, synth.orbit_flexing,
+                                synth.draw_sources(1, seed=1, A=1e-21, fdot=1e-17)[0])):
+        orb = orbf(T0 - 3e5, T0 + DT * N + 3e5)
+        o = oracle.Orbit(orb.t_knots, orb.pos, orb.delays)
+        t0h, hp, hc = synth.gb_input(src, T0, DT, N, p)
+        t = time.perf_counter()
+        oracle.response(p, 2, DT, T0, N, o, o, hp, hc, t0h, src.lam, src.beta, src.psi)
+        s = time.perf_counter() - t
+        out[name] = {"seconds": s, "link_samples_per_s": 6 * N / s, "N": N}
+    N = 65536
+    orb = synth.orbit_static(T0 - 3e5, T0 + DT * N + 3e5)
+    o = oracle.Orbit(orb.t_knots, orb.pos, orb.delays)
+    t0h, hp, hc = synth.gb_input(src1, T0, DT, N, p)
+    g = synth.white_noise((3, N), 1.0)
+    t = time.perf_counter()
+    oracle.response(p, 2, DT, T0, N, o, o, hp, hc, t0h, src1.lam, src1.beta, src1.psi)
+    oracle.backward(p, 2, DT, T0, N, o, o, hp, hc, t0h, src1.lam, src1.beta, src1.psi, g)
+    s = time.perf_counter() - t
+    out["config4_65536"] = {"seconds": s, "link_samples_per_s": 6 * N / s, "N": N, "what": "forward + adjoint"}
     return out
 
 
@@ -503,6 +590,8 @@ def main():
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-configs", action="store_true",
+                    help="also time the FP64 oracle on configs 1, 2 and 4 in full (about a minute)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

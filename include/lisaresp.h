@@ -135,6 +135,9 @@ LR_API int lr_plan_destroy(lr_plan *plan);
 /* Input samples an output sample needs on each side of its own time: an input series that
  * covers [t0 - left*dt, t0 + (n-1)*dt + right*dt] gives every output a full stencil. */
 LR_API int lr_required_margin(const lr_plan *plan, int64_t *left, int64_t *right);
+/* Output samples per CTA tile the plan uses (the descriptor's tile, or the default chosen for it;
+ * lr_plan_autotune may change it).  Errors: LR_ERR_INVALID_ARG for null pointers. */
+LR_API int lr_plan_tile(const lr_plan *plan, int *tile);
 /* Outputs of the plan's span [0, n) whose TDI reads all have full stencils inside that span
  * (Eqs. tdi1/tdi2 with the reads of Sec. "Implementation"): every chained delay of output k,
  * at most tdi_generation-dependent 3 or 7 link delays (the TDI orbit's bound), reads link
@@ -220,6 +223,27 @@ LR_API int lr_graph_destroy(lr_graph *graph);
  * log2 length bucket.  Allocates and frees temporary device buffers; synchronizes `stream`. */
 LR_API int lr_plan_autotune(lr_plan *plan, int64_t n_samples, int use_cache, void *stream, int *tile_out);
 
+/* The tile autotuner for a ragged batch: times the candidate tiles on a synthetic batch with the
+ * given batch's length distribution (up to 48 of its length quantiles, scaled to at most 2^24
+ * outputs in total), each candidate as one batched call (batch tables + persistent fused kernel),
+ * and keeps the fastest in the plan.  Cached like lr_plan_autotune, keyed by GPU, precision,
+ * order, TDI generation, S and the log2 of the batch's 10/50/90 % length quantiles.
+ *   lengths : HOST int64[S], output samples per source (>= 0)
+ * Allocates and frees temporary device buffers; synchronizes `stream`.
+ * Errors: LR_ERR_INVALID_ARG for null pointers or a negative length; LR_ERR_RANGE for S outside
+ * [1, 2^24] or an all-empty batch. */
+LR_API int lr_plan_autotune_batch(lr_plan *plan, int64_t S, const int64_t *lengths, int use_cache, void *stream,
+                                  int *tile_out);
+/* The Lagrange order for a signal band: the smallest compiled odd degree p whose centered read of
+ * a unit complex sinusoid of f_dt cycles per sample (the band edge f_max * dt) is within tol at
+ * every fractional offset (129 offsets in [0, 1]; host arithmetic, weights by direct products of
+ * Sec. "Implementation"'s centered Lagrange polynomials).  The response's own error is this read
+ * error amplified by the projection and TDI cancellations (|y|/|h| ~ 2 pi f L and more), so tol is
+ * the read accuracy the caller needs, not the response's relative error.
+ * Errors: LR_ERR_INVALID_ARG for f_dt outside [0, 0.5) or tol <= 0; LR_ERR_RANGE when no compiled
+ * order reaches tol. */
+LR_API int lr_choose_order(double f_dt, double tol, int *order);
+
 /* Batched forward that allocates no device memory.  Same arguments, results and asynchrony as
  * lr_response_batched, which allocates its per-batch tables on first use; this variant keeps
  * them in fixed device arrays inside the library, for callers that may not allocate device
@@ -301,6 +325,43 @@ LR_API int lr_likelihood_grad_batched(lr_plan *plan, int64_t S, const int64_t *o
 LR_API int lr_backward_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
                                const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
                                const double *g_xyz, double *g_hp, double *g_hc, double *g_sky, void *stream);
+
+/* ------------------------------------------------------------------ multi-GPU partitioning */
+/* Host-only helpers (no device, context or plan needed) for running the response on several GPUs,
+ * one process per GPU, with no collective on the data path.
+ *
+ * Across sources: the sources of a batch are independent.  Length-balanced greedy deal: sources in
+ * order of decreasing length (equal lengths by index) each go to the rank with the smallest total
+ * length so far (ties to the lower rank).  Deterministic, so every rank computes the same deal.
+ *   lengths : HOST int64[S] (>= 0, e.g. output samples per source)
+ *   rank_of : HOST int[S], written with each source's rank
+ *   load    : HOST int64[ranks], written with each rank's total length (may be NULL)
+ * Errors: LR_ERR_INVALID_ARG for S < 0, ranks < 1, null arrays or a negative length. */
+LR_API int lr_partition_sources(int64_t S, const int64_t *lengths, int ranks, int *rank_of, int64_t *load);
+
+/* Across time for one long source: rank `rank` of `ranks` owns outputs [first, first + count) of the
+ * span [0, n) (whole units of `align` outputs, dealt as evenly as possible in rank order, the extra units to
+ * the last ranks: the owned counts differ by at most `align`) and
+ * computes the span [lo, hi): the owned range widened by halo_left / halo_right outputs, rounded
+ * out to multiples of `align` and clamped to [0, n).  Run it as a plan of hi - lo outputs starting at
+ * t0 + lo*dt, with the unsplit run's strain shifted by lo samples (input sample 0 at t0_h + lo*dt;
+ * the same fractional read offsets, so the same arithmetic) covering lr_required_margin around
+ * that span, and keep outputs
+ * first - lo .. first - lo + count - 1: they equal the unsplit run's outputs first .. first + count - 1
+ * when halo_left = *first and halo_right = n - 1 - *last of lr_valid_range (every TDI read of an
+ * owned output then lies inside [lo, hi) or outside [0, n) for both runs), and align is the plan's
+ * tile (the span's tiles are then the unsplit run's tiles).  The only exchange is the replicated
+ * strain halo at set-up.  For the adjoint, give each rank g_xyz on its owned outputs only (zero on
+ * the rest of its span): the ranks' sky-angle gradients then add up to the unsplit one (a sum of
+ * three numbers), and their strain gradients add up where their input windows overlap.
+ * Errors: LR_ERR_INVALID_ARG for a null out, n < 0, negative halos, align < 1 or a rank outside
+ * [0, ranks). */
+typedef struct {
+    int64_t first, count;  /* outputs this rank owns */
+    int64_t lo, hi;        /* output span this rank computes */
+} lr_time_shard;
+LR_API int lr_partition_time(int64_t n, int64_t halo_left, int64_t halo_right, int64_t align, int ranks, int rank,
+                             lr_time_shard *out);
 
 #ifdef __cplusplus
 }

@@ -36,6 +36,10 @@ class lr_sky(ctypes.Structure):
     _fields_ = [("lam", ctypes.c_double), ("beta", ctypes.c_double), ("psi", ctypes.c_double)]
 
 
+class lr_time_shard(ctypes.Structure):
+    _fields_ = [("first", ctypes.c_int64), ("count", ctypes.c_int64), ("lo", ctypes.c_int64), ("hi", ctypes.c_int64)]
+
+
 class lr_plan_desc(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("precision", ctypes.c_int), ("tdi_generation", ctypes.c_int),
                 ("delay_mode", ctypes.c_int), ("dt", ctypes.c_double), ("t0", ctypes.c_double),
@@ -72,11 +76,16 @@ _SIGS = {
     "lr_graph_launch": (_I, [_P, _P]),
     "lr_graph_destroy": (_I, [_P]),
     "lr_plan_autotune": (_I, [_P, _I64, _I, _P, ctypes.POINTER(_I)]),
+    "lr_plan_autotune_batch": (_I, [_P, _I64, _P, _I, _P, ctypes.POINTER(_I)]),
+    "lr_choose_order": (_I, [_D, _D, ctypes.POINTER(_I)]),
     "lr_likelihood": (_I, [_P, _P, _P, _I64, _D, lr_sky, _P, _P, _P, _P, _P]),
     "lr_likelihood_batched": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _P, _P, _P]),
     "lr_log_likelihood": (_I, [_P, _P, _P, _I64, _D, lr_sky, _P, _P, _P, _P, _P]),
     "lr_log_likelihood_batched": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _P, _P, _P]),
     "lr_valid_range": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "lr_plan_tile": (_I, [_P, ctypes.POINTER(_I)]),
+    "lr_partition_sources": (_I, [_I64, _P, _I, _P, _P]),
+    "lr_partition_time": (_I, [_I64, _I64, _I64, _I64, _I, _I, _P]),
     "lr_likelihood_grad": (_I, [_P, _P, _P, _P, _D, _P, _P]),
     "lr_likelihood_grad_batched": (_I, [_P, _I64, _P, _I64, _P, _P, _P, _D, _P, _P]),
 }
@@ -238,6 +247,13 @@ class Plan:
         a, b = ctypes.c_int64(), ctypes.c_int64()
         _check("lr_required_margin", library().lr_required_margin(self._h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    @property
+    def tile(self) -> int:
+        """Output samples per CTA tile in use."""
+        t = ctypes.c_int()
+        _check("lr_plan_tile", library().lr_plan_tile(self._h, ctypes.byref(t)))
+        return t.value
 
     def valid_range(self):
         """(first, last): the outputs whose TDI stencils lie inside [0, n) (inclusive bounds)."""
@@ -403,6 +419,16 @@ class Plan:
         self.desc.tile = t.value
         return t.value
 
+    def autotune_batch(self, lengths, use_cache: bool = True, stream=None) -> int:
+        """Time candidate tile sizes on a synthetic batch with these source lengths' distribution and
+        keep the fastest; returns it."""
+        ln = np.ascontiguousarray(lengths, dtype=np.int64)
+        t = ctypes.c_int(0)
+        _check("lr_plan_autotune_batch", library().lr_plan_autotune_batch(
+            self._h, len(ln), ln.ctypes.data, 1 if use_cache else 0, _stream_handle(stream), ctypes.byref(t)))
+        self.desc.tile = t.value
+        return t.value
+
     def response_batched_graph(self, h_off, out_off, t0h, sky, hp, hc, xyz):
         """Capture the batched call into a replayable CUDA graph (fixed pointers)."""
         S = t0h.numel()
@@ -436,6 +462,34 @@ class Plan:
             _dev64(g_hp, "g_hp", hp.numel()), _dev64(g_hc, "g_hc", hp.numel()), _dev64(g_sky, "g_sky", 3 * S),
             _stream_handle(stream)))
         return g_hp, g_hc, g_sky
+
+
+def partition_sources(lengths, ranks: int):
+    """(rank_of int32 [S], load int64 [ranks]): the library's length-balanced deal of independent
+    sources over ranks (identical on every rank)."""
+    ln = np.ascontiguousarray(lengths, dtype=np.int64)
+    rank_of = np.empty(len(ln), dtype=np.int32)
+    load = np.empty(int(ranks), dtype=np.int64)
+    _check("lr_partition_sources", library().lr_partition_sources(len(ln), ln.ctypes.data, int(ranks),
+                                                                  rank_of.ctypes.data, load.ctypes.data))
+    return rank_of, load
+
+
+def partition_time(n: int, halo_left: int, halo_right: int, align: int, ranks: int, rank: int) -> lr_time_shard:
+    """The library's time split of one source's outputs [0, n): rank `rank` owns [first, first + count)
+    and computes the span [lo, hi)."""
+    out = lr_time_shard()
+    _check("lr_partition_time", library().lr_partition_time(int(n), int(halo_left), int(halo_right), int(align),
+                                                            int(ranks), int(rank), ctypes.byref(out)))
+    return out
+
+
+def choose_order(f_dt: float, tol: float) -> int:
+    """Smallest compiled Lagrange order whose read of a sinusoid at f_dt cycles per sample is within
+    tol (see lr_choose_order)."""
+    o = ctypes.c_int(0)
+    _check("lr_choose_order", library().lr_choose_order(float(f_dt), float(tol), ctypes.byref(o)))
+    return o.value
 
 
 def order_supported(order: int) -> bool:

@@ -56,10 +56,45 @@ __device__ void project_sample64(const FwdParams &P, const SkyConst &S, int64_t 
 // ---------------------------------------------------------------- TDI of one sample
 // X = sum_q D_{chain A up to q} y_link(A,q) - sum_q D_{chain B up to q} y_link(B,q); the
 // delay of term q is the sum (or nesting) of the chain's first q link delays, all at t_n.
+// Constant delays: every delayed read of a term has the same fractional offset, so its weights
+// are plan constants and a read is a plain T-tap dot product.
+template <int T>
+__device__ void tdi_sample64_const(const FwdParams &P, int64_t n, const double *ys, int ystride, int64_t k_lo,
+                                   int ylen, double out[3])
+{
+    const int nl = (int)(n - k_lo);
+    for (int ch = 0; ch < 3; ++ch) {
+        double acc = 0.0;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            double part = ys[c_tdi64.link[ch][c][0] * ystride + nl];
+            for (int q = 1; q <= P.q_terms; ++q) {
+                const int st = nl + P.cd_off[ch][c][q];
+                if (st < 0 || st + T > ylen) {
+                    atomicOr(P.err, ERR_WINDOW);
+                    continue;
+                }
+                const double *s = ys + c_tdi64.link[ch][c][q] * ystride + st;
+                const double *w = P.cd_w + ((ch * 2 + c) * CHAIN_TERMS + q) * T;
+                double r = 0.0;
+#pragma unroll
+                for (int j = 0; j < T; ++j) r = fma(__ldg(w + j), s[j], r);
+                part += r;
+            }
+            acc = c == 0 ? part : acc - part;
+        }
+        out[ch] = acc;
+    }
+}
+
 template <int T>
 __device__ void tdi_sample64(const FwdParams &P, int64_t n, const double *ys, int ystride, int64_t k_lo,
                              int ylen, double out[3])
 {
+    if (P.cd_w) {
+        tdi_sample64_const<T>(P, n, ys, ystride, k_lo, ylen, out);
+        return;
+    }
     double t = P.t0 + (double)n * P.dt;
     double Ls[6];
     orbit_delays(P.to, t, Ls);

@@ -58,6 +58,8 @@ struct lr_plan {
     int64_t lpart_cap;
     // nested-delay table of the mixed kernels ([knots][42], samples)
     double *d_nest;
+    // constant-delay TDI weights of the FP64 kernels ([3][2][8][T]), or null
+    double *d_cdw;
 };
 
 namespace lr {
@@ -257,6 +259,53 @@ int nested_table(lr_plan *p, const lr_orbit *o)
     P.nest_n = nk;
     P.nest_t0 = o->t_first;
     P.nest_inv_dk = 1.0 / o->dk;
+    return LR_OK;
+}
+
+// Constant TDI delays (Sec. TDI with L_ij independent of t, e.g. the equal-arm template): when
+// every delay spline of the TDI orbit is a constant, each chained delay is a constant number of
+// samples, so each delayed read has one fractional offset for all outputs.  Its centered Lagrange
+// weights (Sec. "Implementation", direct products) and its first tap's offset are computed once
+// here; the FP64 kernels then read with a plain dot product.  Nested and summed delays coincide.
+int constant_delay_table(lr_plan *p, const lr_orbit *o)
+{
+    for (int l = 0; l < 6; ++l) {
+        const double c0 = o->coef[(size_t)(9 + l) * 4];
+        for (int k = 0; k < o->nint; ++k) {
+            const double *q = o->coef.data() + ((size_t)k * lr::NSERIES + 9 + l) * 4;
+            if (q[0] != c0 || q[1] != 0.0 || q[2] != 0.0 || q[3] != 0.0) return LR_OK;  // not constant
+        }
+    }
+    const int T = p->T, h = p->h;
+    const lr::TdiTab tab = lr::make_tdi_tab();
+    lr::FwdParams &P = p->base;
+    std::vector<double> w((size_t)3 * 2 * lr::CHAIN_TERMS * T, 0.0);
+    for (int ch = 0; ch < 3; ++ch)
+        for (int c = 0; c < 2; ++c) {
+            double D = 0.0;  // samples
+            P.cd_off[ch][c][0] = 0;
+            for (int q = 1; q < lr::CHAIN_TERMS; ++q) {
+                const int l = tab.pair[ch][c][q];
+                D += o->coef[(size_t)(9 + l) * 4] * P.inv_dt;
+                const double u = -D, fl = std::floor(u), eps = u - fl;
+                P.cd_off[ch][c][q] = (int)fl - h;
+                double *wq = w.data() + ((size_t)(ch * 2 + c) * lr::CHAIN_TERMS + q) * T;
+                for (int a = 0; a < T; ++a) {
+                    double prod = 1.0;
+                    for (int b = 0; b < T; ++b)
+                        if (b != a) prod *= (eps - (double)(b - h)) / (double)(a - b);
+                    wq[a] = prod;
+                }
+            }
+        }
+    cudaError_t e = lr::dev_malloc((void **)&p->d_cdw, sizeof(double) * w.size());
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_cdw, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (p->d_cdw) cudaFree(p->d_cdw);
+        p->d_cdw = nullptr;
+        return cuda_fail(p->ctx, e);
+    }
+    P.cd_w = p->d_cdw;
     return LR_OK;
 }
 
@@ -490,6 +539,7 @@ LR_API int lr_plan_create(lr_ctx *ctx, const lr_plan_desc *d, lr_plan **out)
     p->d_lpart = nullptr;
     p->lpart_cap = 0;
     p->d_nest = nullptr;
+    p->d_cdw = nullptr;
     lr::FwdParams &P = p->base;
     std::memset(&P, 0, sizeof(P));
     P.dt = d->dt;
@@ -555,6 +605,14 @@ LR_API int lr_plan_create(lr_ctx *ctx, const lr_plan_desc *d, lr_plan **out)
             return st;
         }
     }
+    if (d->precision == LR_FP64) {
+        const int st = constant_delay_table(p, d->tdi_orbit);
+        if (st) {
+            cudaFree(p->d_err);
+            delete p;
+            return st;
+        }
+    }
     *out = p;
     return LR_OK;
 }
@@ -570,6 +628,7 @@ LR_API int lr_plan_destroy(lr_plan *plan)
     if (plan->d_htile_off) cudaFree(plan->d_htile_off);
     if (plan->d_lpart) cudaFree(plan->d_lpart);
     if (plan->d_nest) cudaFree(plan->d_nest);
+    if (plan->d_cdw) cudaFree(plan->d_cdw);
     lr::pipe_free(plan->pipe);
     delete plan;
     return LR_OK;
@@ -580,6 +639,13 @@ LR_API int lr_required_margin(const lr_plan *plan, int64_t *left, int64_t *right
     if (!plan || !left || !right) return LR_ERR_INVALID_ARG;
     *left = plan->base.sig_b + plan->base.lproj_b + plan->h + 2;
     *right = plan->base.sig_b + plan->h + 2;
+    return LR_OK;
+}
+
+LR_API int lr_plan_tile(const lr_plan *plan, int *tile)
+{
+    if (!plan || !tile) return LR_ERR_INVALID_ARG;
+    *tile = plan->base.tile;
     return LR_OK;
 }
 

@@ -118,6 +118,12 @@ struct FwdParams {
     double nest_t0, nest_inv_dk;
     double cheb[4][4];      // monomial coefficients of the cubic through 4 Chebyshev nodes on [-1, 1]
     double cheb_node[4];    // the nodes cos((2 i + 1) pi / 8)
+    // constant TDI delays (every delay spline of the TDI orbit constant): per delayed term
+    // (channel, chain, q = 1..7) the Lagrange weights of its fixed fractional offset,
+    // [3][2][8][T] FP64 (q = 0 unused), and the first tap's offset from the output sample;
+    // null when the delays vary (FP64 kernels only)
+    const double *cd_w;
+    int cd_off[3][2][CHAIN_TERMS];
 };
 
 // error-word bits

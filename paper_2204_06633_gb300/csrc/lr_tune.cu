@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 #include <sys/stat.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -79,9 +80,62 @@ void cache_store(const std::string &key, int tile, double ms)
     std::fclose(f);
 }
 
+std::vector<int> tile_candidates(const lr::PlanView &v)
+{
+    std::vector<int> cand;
+    if (v.precision == LR_MIXED) {
+        // the largest tile the shared-memory arrays hold, and smaller ones
+        const int tmax = lr::mx_max_tile(v.base.HL, v.base.HR, v.base.lproj_b, v.order + 1);
+        cand.push_back(tmax);
+        for (int t : {256, 192, 128})
+            if (t < tmax) cand.push_back(t);
+    } else {
+        for (int t : {256, 384, 512, 768, 1024}) cand.push_back(t);
+    }
+    return cand;
+}
+
+// Largest |exp(i w eps) - sum_j w_j(eps) exp(i w j)| over eps in [0, 1) (129 points) for the
+// centered Lagrange read of degree p (nodes j = -(p-1)/2 .. (p+1)/2, weights by direct products):
+// the read error of a unit complex sinusoid of w radians per sample.
+double lagrange_sinusoid_error(int p, double w)
+{
+    const int h = (p - 1) / 2, T = p + 1;
+    double worst = 0.0;
+    for (int k = 0; k <= 128; ++k) {
+        const double eps = k / 128.0;
+        double re = 0.0, im = 0.0;
+        for (int a = 0; a < T; ++a) {
+            const int ja = a - h;
+            double wa = 1.0;
+            for (int b = 0; b < T; ++b)
+                if (b != a) wa *= (eps - (double)(b - h)) / (double)(ja - (b - h));
+            re += wa * std::cos(w * ja);
+            im += wa * std::sin(w * ja);
+        }
+        const double dr = std::cos(w * eps) - re, di = std::sin(w * eps) - im;
+        worst = std::max(worst, std::sqrt(dr * dr + di * di));
+    }
+    return worst;
+}
+
 }  // namespace
 
 extern "C" {
+
+LR_API int lr_choose_order(double f_dt, double tol, int *order)
+{
+    if (!order || !(f_dt >= 0.0) || !(f_dt < 0.5) || !(tol > 0.0) || !std::isfinite(tol)) return LR_ERR_INVALID_ARG;
+    const double w = 2.0 * 3.14159265358979323846 * f_dt;
+    for (int p = 1; p <= 63; p += 2) {
+        if (!lr::order_supported(p)) continue;
+        if (lagrange_sinusoid_error(p, w) <= tol) {
+            *order = p;
+            return LR_OK;
+        }
+    }
+    return LR_ERR_RANGE;
+}
 
 LR_API int lr_response_batched_graph(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
                                      const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
@@ -174,16 +228,7 @@ LR_API int lr_plan_autotune(lr_plan *plan, int64_t n_samples, int use_cache, voi
             return LR_OK;
         }
     }
-    std::vector<int> cand;
-    if (v.precision == LR_MIXED) {
-        // the largest tile the shared-memory arrays hold, and smaller ones in steps of 4 outputs
-        const int tmax = lr::mx_max_tile(v.base.HL, v.base.HR, v.base.lproj_b, v.order + 1);
-        cand.push_back(tmax);
-        for (int t : {256, 192, 128})
-            if (t < tmax) cand.push_back(t);
-    } else {
-        for (int t : {256, 384, 512, 768, 1024}) cand.push_back(t);
-    }
+    std::vector<int> cand = tile_candidates(v);
     // synthetic single-source problem with all the input margins the plan needs
     const int64_t left = v.base.sig_b + v.base.lproj_b + v.order / 2 + 4, right = v.base.sig_b + v.order / 2 + 4;
     const int64_t nh = n_samples + left + right;
@@ -229,6 +274,121 @@ LR_API int lr_plan_autotune(lr_plan *plan, int64_t n_samples, int use_cache, voi
     if (b) cudaEventDestroy(b);
     if (h) cudaFree(h);
     if (out) cudaFree(out);
+    lr::plan_set_tile(plan, best_ms < 1e300 ? best : tile0);
+    if (e != cudaSuccess) return lr::plan_cuda_fail(plan, e);
+    if (best_ms < 1e300 && use_cache) cache_store(key, best, best_ms);
+    *tile_out = best_ms < 1e300 ? best : tile0;
+    return LR_OK;
+}
+
+LR_API int lr_plan_autotune_batch(lr_plan *plan, int64_t S, const int64_t *lengths, int use_cache, void *stream,
+                                  int *tile_out)
+{
+    if (!plan || !lengths || !tile_out) return LR_ERR_INVALID_ARG;
+    if (S < 1 || S > ((int64_t)1 << 24)) return LR_ERR_RANGE;
+    lr::PlanView v;
+    int st = lr::plan_view(plan, &v);
+    if (st) return st;
+    // the batch's length distribution: up to 48 quantiles, scaled so the synthetic batch holds at
+    // most 2^24 outputs (the tile choice depends on the mix of lengths, not on the batch size)
+    std::vector<int64_t> sorted(lengths, lengths + S);
+    for (int64_t x : sorted)
+        if (x < 0) return LR_ERR_INVALID_ARG;
+    std::sort(sorted.begin(), sorted.end());
+    const int64_t k = std::min<int64_t>(S, 48);
+    std::vector<int64_t> lens((size_t)k);
+    double tot = 0.0;
+    for (int64_t i = 0; i < k; ++i) {
+        lens[(size_t)i] = sorted[(size_t)((2 * i + 1) * S / (2 * k))];
+        tot += (double)lens[(size_t)i];
+    }
+    if (tot < 1.0) return LR_ERR_RANGE;
+    const double scale = std::min(1.0, (double)(1 << 24) / tot);
+    const int generation = v.base.q_terms == 3 ? 1 : 2;
+    char sig[160];
+    std::snprintf(sig, sizeof(sig), "|batch%lld_%.0f_%.0f_%.0f", (long long)S, std::log2((double)sorted[(size_t)(S / 10)] + 1),
+                  std::log2((double)sorted[(size_t)(S / 2)] + 1), std::log2((double)sorted[(size_t)(9 * S / 10)] + 1));
+    const std::string key = tune_key(v, generation, 0) + sig;
+    if (use_cache) {
+        int t = cache_lookup(key);
+        if (t > 0 && lr::plan_set_tile(plan, t) == LR_OK) {
+            *tile_out = t;
+            return LR_OK;
+        }
+    }
+    const int64_t left = v.base.sig_b + v.base.lproj_b + v.order / 2 + 4, right = v.base.sig_b + v.order / 2 + 4;
+    std::vector<int64_t> hoff((size_t)k + 1, 0), ooff((size_t)k + 1, 0);
+    std::vector<double> t0h((size_t)k);
+    std::vector<lr_sky> sky((size_t)k);
+    for (int64_t i = 0; i < k; ++i) {
+        const int64_t n = std::max<int64_t>(1, (int64_t)(scale * (double)lens[(size_t)i]));
+        ooff[(size_t)i + 1] = ooff[(size_t)i] + n;
+        hoff[(size_t)i + 1] = hoff[(size_t)i] + n + left + right;
+        t0h[(size_t)i] = v.base.t0 - (double)left * v.base.dt;
+        sky[(size_t)i] = lr_sky{0.3 + 0.1 * (double)i, 0.2, 0.4};
+    }
+    const int64_t nh = hoff[(size_t)k], no = ooff[(size_t)k];
+    double *h = nullptr, *out = nullptr, *d_t0h = nullptr;
+    int64_t *d_off = nullptr, *tables = nullptr;
+    lr_sky *d_sky = nullptr;
+    cudaStream_t cs = (cudaStream_t)stream;
+    cudaError_t e = lr::dev_malloc((void **)&h, sizeof(double) * (size_t)nh);
+    if (e == cudaSuccess) e = lr::dev_malloc((void **)&out, sizeof(double) * 3 * (size_t)no);
+    if (e == cudaSuccess) e = lr::dev_malloc((void **)&d_off, sizeof(int64_t) * 2 * (size_t)(k + 1));
+    if (e == cudaSuccess) e = lr::dev_malloc((void **)&d_t0h, sizeof(double) * (size_t)k);
+    if (e == cudaSuccess) e = lr::dev_malloc((void **)&d_sky, sizeof(lr_sky) * (size_t)k);
+    if (e == cudaSuccess) e = lr::dev_malloc((void **)&tables, (sizeof(int64_t) + sizeof(lr::SkyConst)) * (size_t)(k + 1));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h, 0, sizeof(double) * (size_t)nh, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, hoff.data(), sizeof(int64_t) * (size_t)(k + 1), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_off + k + 1, ooff.data(), sizeof(int64_t) * (size_t)(k + 1), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_t0h, t0h.data(), sizeof(double) * (size_t)k, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_sky, sky.data(), sizeof(lr_sky) * (size_t)k, cudaMemcpyHostToDevice, cs);
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    const int tile0 = v.base.tile;
+    int best = tile0;
+    double best_ms = 1e300;
+    const std::vector<int> cand = tile_candidates(v);
+    lr::SkyConst *skyc = v.precision == LR_MIXED ? reinterpret_cast<lr::SkyConst *>(tables + k + 1) : nullptr;
+    for (size_t i = 0; e == cudaSuccess && i < cand.size(); ++i) {
+        if (lr::plan_set_tile(plan, cand[i]) != LR_OK) continue;
+        lr::PlanView w;
+        lr::plan_view(plan, &w);
+        lr::FwdParams P = w.base;
+        P.src.skyc = skyc;
+        P.src.h_off = d_off;
+        P.src.out_off = d_off + k + 1;
+        P.src.t0h = d_t0h;
+        P.src.sky = d_sky;
+        P.src.tile_off = tables;
+        P.src.S = k;
+        P.hp = h;
+        P.hc = h;
+        P.out = out;
+        P.total_tiles = -1;
+        // one batched call = the batch tables and the persistent fused kernel, as lr_response_batched
+        auto call = [&]() {
+            int le = lr::launch_batch_tables(P.src.out_off, d_sky, k, P.tile, tables, skyc, P.err, cs);
+            return le ? le : lr::launch_forward(w.precision, lr::KIND_FUSED, w.order, P, w.threads, w.sms, cs);
+        };
+        if (call()) continue;
+        cudaEventRecord(a, cs);
+        for (int r = 0; r < 3; ++r) call();
+        cudaEventRecord(b, cs);
+        e = cudaEventSynchronize(b);
+        float ms = 0.0f;
+        if (e == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+        if (e == cudaSuccess && ms / 3.0 < best_ms) {
+            best_ms = ms / 3.0;
+            best = cand[i];
+        }
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    for (void *p : {(void *)h, (void *)out, (void *)d_t0h, (void *)d_off, (void *)tables, (void *)d_sky})
+        if (p) cudaFree(p);
     lr::plan_set_tile(plan, best_ms < 1e300 ? best : tile0);
     if (e != cudaSuccess) return lr::plan_cuda_fail(plan, e);
     if (best_ms < 1e300 && use_cache) cache_store(key, best, best_ms);

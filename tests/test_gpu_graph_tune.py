@@ -102,3 +102,28 @@ def test_graph_survives_a_larger_batch_on_the_same_plan(setup, precision):
     ref = plan.response_batched(*args)
     plan.check()
     assert torch.equal(xyz, ref)
+
+
+@pytest.mark.parametrize("precision,rel", [(lr.FP64, 1e-12), (lr.MIXED, 1e-6)])
+def test_batch_autotune_picks_a_candidate_and_keeps_results(setup, precision, rel, tmp_path):
+    """The batch tuner times candidate tiles on the ragged batch's length mix; the tuned plan's
+    results match the default plan's (bit for bit in FP64, where the tile does not enter the
+    arithmetic; within the mixed tolerance otherwise) and the choice is cached."""
+    ctx, o = setup
+    os.environ["LR_AUTOTUNE_CACHE"] = str(tmp_path / "tune.txt")
+    lens = [3000, 12000, 777, 65536, 0, 40000]
+    args = make_batch(lens, 45)
+    ref_plan = lr.Plan(ctx, P, 1, DT, o, t0=T0, precision=precision)
+    ref = ref_plan.response_batched(*args)
+    plan = lr.Plan(ctx, P, 1, DT, o, t0=T0, precision=precision)
+    tile = plan.autotune_batch(lens, use_cache=True)
+    assert tile == plan.tile and tile > 0
+    got = plan.response_batched(*args)
+    plan.check()
+    if precision == lr.FP64:
+        assert torch.equal(got, ref)
+    else:
+        assert float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref)) <= rel
+    assert "|batch6_" in open(tmp_path / "tune.txt").read()
+    again = lr.Plan(ctx, P, 1, DT, o, t0=T0, precision=precision)
+    assert again.autotune_batch(lens, use_cache=True) == tile

@@ -189,7 +189,7 @@ def test_bench_workload_sampled(ctx):
     import bench
 
     p = 25
-    lens, srcs = bench.workload(0, 1024)
+    lens, srcs = bench.workload(0, 1, 1024)
     h_off, out_off, t0h, sky_, hp, hc = bench.build_inputs(lens, srcs, p)
     orb = synth.orbit_flexing(T0 - 3e5, T0 + DT * int(lens.max()) + 3e5)
     o = Pair(ctx, orb)

@@ -1,6 +1,7 @@
-"""The multi-rank benchmark path on CPU (gloo, world size 2): each rank draws its own batch
-(weak scaling, no data-path collective) and the job throughput is the sum of all ranks'
-samples over the slowest rank's time, identical on every rank."""
+"""The multi-rank benchmark path on CPU (gloo, world size 2): the job's batch (world x 8 sources)
+is dealt over the ranks by the library's length-balanced partition (weak scaling, no data-path
+collective), and the job throughput is the sum of all ranks' samples over the slowest rank's time,
+identical on every rank."""
 import os
 import socket
 
@@ -22,11 +23,11 @@ def _worker(rank, ws, port, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws),
                       LOCAL_RANK=str(rank))
     dist.init_process_group("gloo", rank=rank, world_size=ws)
-    lens, srcs = bench.workload(rank, 8)
+    lens, srcs = bench.workload(rank, ws, 8)
     samples = int(lens.sum())
     ms_local = 100.0 + 50.0 * rank          # rank 1 is the slow one
     value, ms, total = bench.job_throughput(samples, ms_local)
-    out[rank] = (value, ms, total, samples, float(srcs[0].f))
+    out[rank] = (value, ms, total, samples, sorted(float(s.f) for s in srcs))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -44,8 +45,11 @@ def test_two_rank_job_throughput():
     assert ms == 150.0                          # max over ranks
     assert total == r0[3] + r1[3]               # sum over ranks
     assert np.isclose(value, 6.0 * total / 0.150)
-    # the ranks' batches are different draws
-    assert r0[3] != r1[3] and r0[4] != r1[4]
+    # the ranks' shares are disjoint and together the whole batch, balanced within one source
+    glens, gsrcs = bench.workload(0, 1, 2 * 8)
+    assert sorted(r0[4] + r1[4]) == sorted(float(s.f) for s in gsrcs)
+    assert total == glens.sum()
+    assert abs(r0[3] - r1[3]) <= glens.max()
 
 
 def test_single_process_identity():
