@@ -357,6 +357,55 @@ def run_ours(args):
         like = {"value": link_samples / (ms_like * 1e-3), "unit": "link-samples/s", "ms_per_step": ms_like,
                 "steps": args.steps, "warmup": args.warmup, "ms_response_per_step": ms_step,
                 "api": "lr_likelihood_batched (per source <d|h>, <h|h> over A, E, T; X, Y, Z not written)"}
+        # the same batch with the Galactic-binary strain generated on chip (no strain input):
+        # the response, and the sampler's step (parameters in, one log-likelihood per source out)
+        gb_h = np.array([[s.A, s.f, s.fdot, s.fddot_value(), s.phi0, s.iota] for s in srcs])
+        d_gb = torch.tensor(gb_h, device=dev)
+        logl = torch.empty(args.sources, dtype=torch.float64, device=dev)
+
+        def ev_time(f, n):
+            for _ in range(args.warmup):
+                f()
+            torch.cuda.synchronize()
+            barrier()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(n):
+                f()
+            b.record(stream)
+            torch.cuda.synchronize()
+            plan.check(stream)
+            return max_over_ranks(a.elapsed_time(b) / n)
+
+        ms_gen = ev_time(lambda: plan.response_gb_batched(d_ooff, d_gb, d_sky, xyz=d_xyz, stream=stream), args.steps)
+        ms_genl = ev_time(lambda: plan.log_likelihood_gb_batched(d_ooff, d_gb, d_sky, data, out=logl, stream=stream),
+                          args.steps)
+        # end to end: pinned host parameters in, the log-likelihoods back in host memory, each step
+        gb_pin = torch.from_numpy(np.ascontiguousarray(gb_h)).pin_memory()
+        sky_pin = torch.from_numpy(np.ascontiguousarray(sky)).pin_memory()
+        logl_pin = torch.empty(args.sources, dtype=torch.float64).pin_memory()
+
+        def gen_e2e_step():
+            d_gb.copy_(gb_pin, non_blocking=True)
+            d_sky.copy_(sky_pin, non_blocking=True)
+            plan.log_likelihood_gb_batched(d_ooff, d_gb, d_sky, data, out=logl, stream=stream)
+            logl_pin.copy_(logl, non_blocking=True)
+            stream.synchronize()
+
+        gen_e2e_step()
+        barrier()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            gen_e2e_step()
+        ms_gen_e2e = max_over_ranks((time.perf_counter() - t) * 1e3 / args.steps)
+        plan.check(stream)
+        like["generated_strain"] = {
+            "response_ms_per_step": ms_gen, "response_value": link_samples / (ms_gen * 1e-3),
+            "loglike_ms_per_step": ms_genl, "loglike_value": link_samples / (ms_genl * 1e-3), "unit": "link-samples/s",
+            "api": "lr_response_gb_batched / lr_log_likelihood_gb_batched (Galactic binaries generated on chip)",
+            "e2e": {"value": link_samples / (ms_gen_e2e * 1e-3), "unit": "link-samples/s", "ms_per_step": ms_gen_e2e,
+                    "h2d_bytes_per_step": int(gb_pin.numel() * 8 + sky_pin.numel() * 8),
+                    "d2h_bytes_per_step": int(logl_pin.numel() * 8)}}
         del data
 
     # the same batch in plain FP64 on the same GPU (the comparison the metric names)

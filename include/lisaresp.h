@@ -77,6 +77,14 @@ typedef struct lr_plan lr_plan;
  * k = -e_r, u = -e_phi, v = -e_theta of the SSB spherical basis (Sec. "Reference frames"). */
 typedef struct { double lam, beta, psi; } lr_sky;
 
+/* Galactic-binary parameters (Sec. "Template generation"): amplitude A, initial frequency f0 (Hz)
+ * and its derivatives fdot (Hz/s), fddot (Hz/s^2; the paper takes 11 fdot^2 / (3 f0)), initial
+ * phase phi0 and inclination iota (rad), with t measured on the library's time axis.  The
+ * polarisations are h+ = A (1 + cos^2 iota) cos Phi and hx = 2 A cos iota sin Phi,
+ * Phi = 2 pi (f0 t + fdot t^2 / 2 + fddot t^3 / 6) + phi0: the un-rotated inputs of the response
+ * (psi is the sky's; pass -A for the paper's SSB sign). */
+typedef struct { double A, f0, fdot, fddot, phi0, iota; } lr_gb;
+
 typedef struct {
     int order;            /* Lagrange degree p: odd, 1 <= p <= 63 (a compiled subset; see lr_order_supported) */
     int precision;        /* LR_FP64 or LR_MIXED */
@@ -262,6 +270,32 @@ LR_API int lr_choose_order(double f_dt, double tol, int *order);
 LR_API int lr_response_batched_noalloc(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
                                        const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
                                        double *xyz, void *stream);
+
+/* ------------------------------------------------------------------ generated strain */
+/* The Galactic-binary waveform of Sec. "Template generation" generated on the device instead of
+ * read from arrays: the fused kernels compute the strain window each tile reads directly from the
+ * parameters (lr_gb), on the output grid t0 + i dt at every index i (no zero extension: the
+ * waveform exists at all times), so no strain crosses HBM.  The phase is formed in double-double
+ * and reduced modulo one cycle before the FP64 sincos (a few 1e-16 rad at any t and f0).
+ *
+ * h+, hx [n] at t0 + j dt into DEVICE arrays, the same generator as the fused kernels.  Errors:
+ * LR_ERR_INVALID_ARG for null pointers or n < 0, LR_ERR_NONFINITE for a non-finite parameter. */
+LR_API int lr_gb_polarisations(const lr_gb *gb /* HOST */, double t0, double dt, int64_t n, double *hp, double *hc,
+                               void *stream);
+/* Fused response of one Galactic binary over the plan's span: xyz DEVICE [3][plan.n].  Errors as
+ * lr_response; LR_ERR_NONFINITE for a non-finite parameter. */
+LR_API int lr_response_gb(lr_plan *plan, lr_gb gb, lr_sky sky, double *xyz, void *stream);
+/* Batched: S sources with output offsets out_off (DEVICE int64[S+1]), parameters gb (DEVICE lr_gb[S])
+ * and sky (DEVICE lr_sky[S]); xyz as lr_response_batched.  Non-finite parameters give non-finite
+ * outputs for that source.  Errors as lr_response_batched. */
+LR_API int lr_response_gb_batched(lr_plan *plan, int64_t S, const int64_t *out_off, const lr_gb *gb,
+                                  const lr_sky *sky, double *xyz, void *stream);
+/* Per-source log-likelihood <d|h> - <h|h>/2 of generated templates (the sampler's step: parameters
+ * in, one number per walker out): logl DEVICE double[S]; data, n_total, weights, xyz as
+ * lr_log_likelihood_batched. */
+LR_API int lr_log_likelihood_gb_batched(lr_plan *plan, int64_t S, const int64_t *out_off, const lr_gb *gb,
+                                        const lr_sky *sky, const double *data, int64_t n_total,
+                                        const double *weights, double *logl, double *xyz, void *stream);
 
 /* ------------------------------------------------------------------ likelihood */
 /* Fused likelihood epilogue of the forward (the log-likelihood of Eq. like,

@@ -101,6 +101,7 @@ def _load():
             "orc_sky_gradient": (I, [I, D, D, I64, P, dp, dp, I64, D, D, D, D, dp, dp]),
             "orc_sky_gradient_abs": (I, [I, D, D, I64, P, dp, dp, I64, D, D, D, D, dp, dp]),
             "orc_aet": (None, [dp, I64, dp]),
+            "orc_gb_polarisations": (None, [D, D, D, D, D, D, D, D, I64, dp, dp]),
             "orc_like_inner": (None, [dp, dp, I64, dp, dp]),
         }
         for name, (res, args) in sig.items():
@@ -126,6 +127,8 @@ def _load_quad():
         lib.orq_response.restype, lib.orq_response.argtypes = I, common + [P]
         lib.orq_backward.restype, lib.orq_backward.argtypes = I, common + [P, P, P, P]
         lib.orq_response_at.restype, lib.orq_response_at.argtypes = I, common + [P, I64, P]
+        lib.orq_gb_polarisations.restype = None
+        lib.orq_gb_polarisations.argtypes = [D, D, D, D, D, D, D, D, I64, P, P]
         _libq = lib
         return lib
 
@@ -351,6 +354,19 @@ def backward(p, gen, dt, t0, n, porb, torb, hp, hc, t0h, lam, beta, psi, gxyz, d
     if with_scale:
         return ghp, ghc, gsky, sky_gradient(p, dt, t0, n, porb, hp, hc, t0h, lam, beta, psi, gy, absval=True)
     return ghp, ghc, gsky
+
+
+# ---------------------------------------------------------------- Galactic binary
+def gb_polarisations(A, f0, fdot, fddot, phi0, iota, t0, dt, n, quad: bool = False):
+    """(h+, hx) [n] of a Galactic binary at t0 + j dt (Sec. "Template generation"; un-rotated, psi
+    applied by the response); quad=True evaluates the same formula in binary128."""
+    hp, hc = np.empty(int(n)), np.empty(int(n))
+    args = [float(A), float(f0), float(fdot), float(fddot), float(phi0), float(iota), float(t0), float(dt), int(n)]
+    if quad:
+        _load_quad().orq_gb_polarisations(*args, hp.ctypes.data, hc.ctypes.data)
+    else:
+        _load().orc_gb_polarisations(*args, _dp(hp), _dp(hc))
+    return hp, hc
 
 
 # ---------------------------------------------------------------- likelihood

@@ -848,6 +848,27 @@ int orc_sky_gradient_abs(int p, double dt, double t0, int64_t N, const void *por
     return 0;
 }
 
+/* ------------------------------------------------------------------ Galactic binary */
+/* Polarisations of a Galactic binary at t = t0 + j dt, j = 0 .. n-1 (Sec. "Template generation"):
+ * the source-frame waveform h+^S = A cos Phi, hx^S = A sin Phi with
+ * Phi(t) = 2 pi (f0 t + fdot t^2 / 2 + fddot t^3 / 6) + phi0, weighted by the inclination factors
+ * (1 + cos^2 iota) and 2 cos iota of the transform to the SSB frame.  The polarisation angle psi of
+ * that transform is applied by the response (the 2 psi rotation of the antenna patterns), and the
+ * transform's overall minus sign is the caller's (the library's inputs are the un-rotated
+ * polarisations).  fddot is given (the paper takes 11 fdot^2 / (3 f0)). */
+void orc_gb_polarisations(double A, double f0, double fdot, double fddot, double phi0, double iota,
+                          double t0, double dt, int64_t n, double *hp, double *hc)
+{
+    const double pi = 4.0 * atan(1.0);
+    const double ci = cos(iota);
+    for (int64_t j = 0; j < n; ++j) {
+        double t = t0 + (double)j * dt;
+        double ph = 2.0 * pi * (f0 * t + 0.5 * fdot * t * t + fddot * t * t * t / 6.0) + phi0;
+        hp[j] = A * (1.0 + ci * ci) * cos(ph);
+        hc[j] = 2.0 * A * ci * sin(ph);
+    }
+}
+
 /* ------------------------------------------------------------------ likelihood
  * Uncorrelated TDI channels (Sec. "Time-delay interferometry", the A, E, T combinations of
  * X, Y, Z): A = (Z - X)/sqrt(2), E = (X - 2Y + Z)/sqrt(6), T = (X + Y + Z)/sqrt(3).

@@ -29,6 +29,7 @@
 #define fabs fabsf128
 #define sin sinf128
 #define cos cosf128
+#define atan atanf128
 #include "lr_oracle.c"
 #undef double
 #undef sqrt
@@ -37,6 +38,7 @@
 #undef fabs
 #undef sin
 #undef cos
+#undef atan
 
 #define ORQ_API __attribute__((visibility("default")))
 
@@ -149,4 +151,21 @@ ORQ_API int orq_response_at(int p, int gen, int delay_mode, double dt, double t0
     free(qhc);
     free(x);
     return st;
+}
+
+/* Galactic binary polarisations [n] at t0 + j dt (the oracle's formula in binary128, rounded once) */
+ORQ_API void orq_gb_polarisations(double A, double f0, double fdot, double fddot, double phi0, double iota,
+                                  double t0, double dt, int64_t n, double *hp, double *hc)
+{
+    q_t *a = (q_t *)malloc(sizeof(q_t) * (size_t)(n > 0 ? n : 1)), *b = (q_t *)malloc(sizeof(q_t) * (size_t)(n > 0 ? n : 1));
+    if (!a || !b) {
+        free(a);
+        free(b);
+        return;
+    }
+    orc_gb_polarisations((q_t)A, (q_t)f0, (q_t)fdot, (q_t)fddot, (q_t)phi0, (q_t)iota, (q_t)t0, (q_t)dt, n, a, b);
+    orq_narrow(a, n, hp);
+    orq_narrow(b, n, hc);
+    free(a);
+    free(b);
 }

@@ -36,6 +36,11 @@ class lr_sky(ctypes.Structure):
     _fields_ = [("lam", ctypes.c_double), ("beta", ctypes.c_double), ("psi", ctypes.c_double)]
 
 
+class lr_gb(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_double), ("f0", ctypes.c_double), ("fdot", ctypes.c_double),
+                ("fddot", ctypes.c_double), ("phi0", ctypes.c_double), ("iota", ctypes.c_double)]
+
+
 class lr_time_shard(ctypes.Structure):
     _fields_ = [("first", ctypes.c_int64), ("count", ctypes.c_int64), ("lo", ctypes.c_int64), ("hi", ctypes.c_int64)]
 
@@ -84,6 +89,10 @@ _SIGS = {
     "lr_log_likelihood_batched": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _P, _P, _P]),
     "lr_valid_range": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "lr_plan_tile": (_I, [_P, ctypes.POINTER(_I)]),
+    "lr_gb_polarisations": (_I, [ctypes.POINTER(lr_gb), _D, _D, _I64, _P, _P, _P]),
+    "lr_response_gb": (_I, [_P, lr_gb, lr_sky, _P, _P]),
+    "lr_response_gb_batched": (_I, [_P, _I64, _P, _P, _P, _P, _P]),
+    "lr_log_likelihood_gb_batched": (_I, [_P, _I64, _P, _P, _P, _P, _I64, _P, _P, _P, _P]),
     "lr_partition_sources": (_I, [_I64, _P, _I, _P, _P]),
     "lr_partition_time": (_I, [_I64, _I64, _I64, _I64, _I, _I, _P]),
     "lr_likelihood_grad": (_I, [_P, _P, _P, _P, _D, _P, _P]),
@@ -161,6 +170,23 @@ def _host(a, dtype, name: str, numel: int | None = None):
     if numel is not None and arr.size != numel:
         raise ValueError(f"{name} has {arr.size} elements, expected {numel}")
     return arr.ctypes.data, arr
+
+
+def _gb(gb) -> lr_gb:
+    if isinstance(gb, lr_gb):
+        return gb
+    return lr_gb(*[float(x) for x in gb])
+
+
+def gb_polarisations(gb, t0: float, dt: float, n: int, device="cuda", stream=None):
+    """(h+, hx) of a Galactic binary at t0 + j dt, generated by the library's device generator."""
+    hp = torch.empty(int(n), dtype=torch.float64, device=device)
+    hc = torch.empty(int(n), dtype=torch.float64, device=device)
+    g = _gb(gb)
+    _check("lr_gb_polarisations", library().lr_gb_polarisations(ctypes.byref(g), float(t0), float(dt), int(n),
+                                                                _dev64(hp, "hp"), _dev64(hc, "hc"),
+                                                                _stream_handle(stream)))
+    return hp, hc
 
 
 def _sky(sky) -> lr_sky:
@@ -289,6 +315,38 @@ class Plan:
             self._h, _dev64(hp, "hp"), _dev64(hc, "hc", hp.numel()), hp.numel(), float(t0h), _sky(sky),
             _dev64(xyz, "xyz", 3 * self.n), _stream_handle(stream)))
         return xyz
+
+    def response_gb(self, gb, sky, xyz=None, stream=None):
+        """Fused response of a Galactic binary generated on the device: gb = (A, f0, fdot, fddot,
+        phi0, iota), sky = (lambda, beta, psi); X, Y, Z over the plan's span."""
+        xyz = xyz if xyz is not None else torch.empty((3, self.n), dtype=torch.float64, device="cuda")
+        _check("lr_response_gb", library().lr_response_gb(self._h, _gb(gb), _sky(sky), _dev64(xyz, "xyz", 3 * self.n),
+                                                          _stream_handle(stream)))
+        return xyz
+
+    def response_gb_batched(self, out_off, gb, sky, xyz=None, stream=None):
+        """out_off int64 CUDA [S+1]; gb float64 CUDA [S][6] (A, f0, fdot, fddot, phi0, iota);
+        sky float64 CUDA [S][3]."""
+        S = sky.numel() // 3
+        total = int(out_off[-1].item()) if xyz is None else xyz.numel() // 3
+        xyz = self._out(xyz, (3 * total,), sky)
+        _check("lr_response_gb_batched", library().lr_response_gb_batched(
+            self._h, S, _devi64(out_off, "out_off", S + 1), _dev64(gb, "gb", 6 * S), _dev64(sky, "sky", 3 * S),
+            _dev64(xyz, "xyz"), _stream_handle(stream)))
+        return xyz
+
+    def log_likelihood_gb_batched(self, out_off, gb, sky, data, weights=(1.0, 1.0, 1.0), xyz=None, out=None,
+                                  stream=None):
+        """Per-source <d|h> - <h|h>/2 of generated Galactic binaries, float64 CUDA [S]."""
+        S = sky.numel() // 3
+        n_total = data.numel() // 3
+        out = self._out(out, (S,), sky)
+        w = (ctypes.c_double * 3)(*[float(x) for x in weights])
+        _check("lr_log_likelihood_gb_batched", library().lr_log_likelihood_gb_batched(
+            self._h, S, _devi64(out_off, "out_off", S + 1), _dev64(gb, "gb", 6 * S), _dev64(sky, "sky", 3 * S),
+            _dev64(data, "data", 3 * n_total), n_total, ctypes.addressof(w), _dev64(out, "logl", S),
+            _dev64(xyz, "xyz", 3 * n_total) if xyz is not None else None, _stream_handle(stream)))
+        return out
 
     def backward(self, hp, hc, t0h, sky, g_xyz, g_hp=None, g_hc=None, g_sky=None, stream=None):
         g_hp = self._out(g_hp, hp.shape, hp)

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "lr_gb.cuh"
 #include "lr_internal.h"
 
 namespace lr {
@@ -69,6 +70,7 @@ struct TileInfo {
     double *out;      // base of this source's output block
     const double *yin;
     const double *dat;  // base of this source's A, E, T data (likelihood launches), else null
+    GbConst gb;         // generated strain: the source's Galactic-binary constants
     int ok;
 };
 
@@ -101,6 +103,7 @@ __device__ inline TileInfo tile_info(const FwdParams &P, int64_t g, int ochan)
         ti.yin = P.yin;
         ti.dat = P.like.data;
         ti.n0 = g * P.tile;
+        if (P.gen_strain) ti.gb = make_gb(P.src.gb1);
     } else {
         const int64_t *to = P.src.tile_off;
         int64_t lo = 0, hi = P.src.S;  // find s with to[s] <= g < to[s+1]
@@ -109,12 +112,18 @@ __device__ inline TileInfo tile_info(const FwdParams &P, int64_t g, int ochan)
             if (__ldg(to + mid) <= g) lo = mid; else hi = mid;
         }
         int64_t s = lo;
-        int64_t ho = __ldg(P.src.h_off + s), ho1 = __ldg(P.src.h_off + s + 1);
+        int64_t ho = 0, ho1 = 0;
+        if (P.gen_strain) {
+            ti.gb = make_gb(P.src.gb[s]);
+        } else {
+            ho = __ldg(P.src.h_off + s);
+            ho1 = __ldg(P.src.h_off + s + 1);
+        }
         int64_t oo = __ldg(P.src.out_off + s), oo1 = __ldg(P.src.out_off + s + 1);
         ti.N = oo1 - oo;
         ti.nh = ho1 - ho;
         if (ti.N < 0 || ti.nh < 0) ti.ok = 0;
-        ti.t0h = __ldg(P.src.t0h + s);
+        ti.t0h = P.gen_strain ? P.t0 : __ldg(P.src.t0h + s);
         ti.sky = P.src.sky[s];
         ti.hp = P.hp + ho;
         ti.hc = P.hc + ho;
@@ -122,6 +131,10 @@ __device__ inline TileInfo tile_info(const FwdParams &P, int64_t g, int ochan)
         ti.yin = P.yin ? P.yin + 6 * oo : nullptr;
         ti.dat = like_data(P, oo, oo1);
         ti.n0 = (g - __ldg(to + s)) * P.tile;
+    }
+    if (P.gen_strain) {
+        ti.nh = GEN_STRAIN_LEN;
+        ti.t0h = P.t0;
     }
     int64_t rem = ti.N - ti.n0;
     ti.nb = rem < P.tile ? rem : P.tile;

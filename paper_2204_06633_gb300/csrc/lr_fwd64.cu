@@ -142,6 +142,19 @@ __device__ inline void stage(double *dst, const double *src, int64_t lo, int len
     }
 }
 
+// the strain window of a tile: staged from the caller's arrays, or generated (Galactic binary on
+// the output grid, strain index = output index)
+__device__ inline void stage_strain(const FwdParams &P, const TileInfo &ti, double *hwp, double *hwc, int64_t lo,
+                                    int len)
+{
+    if (P.gen_strain) {
+        for (int j = threadIdx.x; j < len; j += blockDim.x) gb_strain(ti.gb, P.t0, P.dt, lo + j, hwp[j], hwc[j]);
+    } else {
+        stage(hwp, ti.hp, lo, len, ti.nh);
+        stage(hwc, ti.hc, lo, len, ti.nh);
+    }
+}
+
 // ---------------------------------------------------------------- kernels
 template <int T>
 __global__ void __launch_bounds__(256) k_fused64(FwdParams P)
@@ -168,8 +181,7 @@ __global__ void __launch_bounds__(256) k_fused64(FwdParams P)
             int64_t w_lo;
             int wlen;
             strain_window(P, T, k_lo, ny, u0, &w_lo, &wlen);
-            stage(hwp, ti.hp, w_lo, wlen, ti.nh);
-            stage(hwc, ti.hc, w_lo, wlen, ti.nh);
+            stage_strain(P, ti, hwp, hwc, w_lo, wlen);
             __syncthreads();
             for (int j = threadIdx.x; j < ny; j += blockDim.x) {
                 int64_t k = k_lo + j;
@@ -227,8 +239,7 @@ __global__ void __launch_bounds__(256) k_project64(FwdParams P)
             int64_t w_lo;
             int wlen;
             strain_window(P, T, ti.n0, ny, u0, &w_lo, &wlen);
-            stage(hwp, ti.hp, w_lo, wlen, ti.nh);
-            stage(hwc, ti.hc, w_lo, wlen, ti.nh);
+            stage_strain(P, ti, hwp, hwc, w_lo, wlen);
             __syncthreads();
             for (int j = threadIdx.x; j < ny; j += blockDim.x) {
                 int64_t k = ti.n0 + j;

@@ -304,6 +304,7 @@ __device__ inline void mx_tile(const FwdParams &P, int64_t g, int ochan, int64_t
         ti.dat = P.like.data;
         ti.n0 = g * P.tile;
         sk = P.src.skyc1;
+        if (P.gen_strain) ti.gb = make_gb(P.src.gb1);
     } else {
         const int64_t *to = P.src.tile_off;
         const int64_t S = P.src.S;
@@ -322,12 +323,18 @@ __device__ inline void mx_tile(const FwdParams &P, int64_t g, int ochan, int64_t
         }
         const int64_t s = lo;
         s_hint = s;
-        const int64_t ho = __ldg(P.src.h_off + s), ho1 = __ldg(P.src.h_off + s + 1);
+        int64_t ho = 0, ho1 = 0;
+        if (P.gen_strain) {
+            ti.gb = make_gb(P.src.gb[s]);
+        } else {
+            ho = __ldg(P.src.h_off + s);
+            ho1 = __ldg(P.src.h_off + s + 1);
+        }
         const int64_t oo = __ldg(P.src.out_off + s), oo1 = __ldg(P.src.out_off + s + 1);
         ti.N = oo1 - oo;
         ti.nh = ho1 - ho;
         if (ti.N < 0 || ti.nh < 0) ti.ok = 0;
-        ti.t0h = __ldg(P.src.t0h + s);
+        ti.t0h = P.gen_strain ? P.t0 : __ldg(P.src.t0h + s);  // no strain arrays when generated
         ti.sky = P.src.sky[s];
         ti.hp = P.hp + ho;
         ti.hc = P.hc + ho;
@@ -336,6 +343,10 @@ __device__ inline void mx_tile(const FwdParams &P, int64_t g, int ochan, int64_t
         ti.dat = like_data(P, oo, oo1);
         ti.n0 = (g - __ldg(to + s)) * P.tile;
         sk = P.src.skyc[s];
+    }
+    if (P.gen_strain) {  // the waveform on the output grid, at every index
+        ti.nh = GEN_STRAIN_LEN;
+        ti.t0h = P.t0;
     }
     const int64_t rem = ti.N - ti.n0;
     ti.nb = rem < P.tile ? rem : P.tile;
@@ -1203,8 +1214,14 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
             unsigned long long mx = 0ull;
             for (int j = tid; j < wlen; j += blockDim.x) {
                 const int64_t i = ts.k_lo + woff + j;
-                const bool in = i >= 0 && i < ts.ti.nh;
-                const double a = in ? __ldg(ts.ti.hp + i) : 0.0, b = in ? __ldg(ts.ti.hc + i) : 0.0;
+                double a, b;
+                if (P.gen_strain) {  // the Galactic binary generated at t0 + i dt
+                    gb_strain(ts.ti.gb, P.t0, P.dt, i, a, b);
+                } else {
+                    const bool in = i >= 0 && i < ts.ti.nh;
+                    a = in ? __ldg(ts.ti.hp + i) : 0.0;
+                    b = in ? __ldg(ts.ti.hc + i) : 0.0;
+                }
                 pf[j] = a;
                 pf[MX_WCAP + j] = b;
                 mx = max(mx, max(abs_bits(a), abs_bits(b)));

@@ -797,11 +797,18 @@ LR_API int lr_response(lr_plan *plan, const double *hp, const double *hc, int64_
     return launch_single(plan, lr::KIND_FUSED, P, stream);
 }
 
-LR_API int lr_response_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
-                               const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
-                               double *xyz, void *stream)
+}  // extern "C"
+
+namespace {
+
+// the batched fused launch; gb != null: Galactic binaries generated on the device (h_off, t0_h,
+// hp, hc unused)
+int response_batched_impl(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off, const double *t0_h,
+                          const lr_sky *sky, const double *hp, const double *hc, const lr_gb *gb, double *xyz,
+                          void *stream)
 {
-    if (!plan || !h_off || !out_off || !t0_h || !sky || !hp || !hc || !xyz) return LR_ERR_INVALID_ARG;
+    if (!plan || !out_off || !sky || !xyz) return LR_ERR_INVALID_ARG;
+    if (!gb && (!h_off || !t0_h || !hp || !hc)) return LR_ERR_INVALID_ARG;
     if (S < 1) return LR_ERR_INVALID_ARG;
     if (S > (int64_t)1 << 24) return LR_ERR_RANGE;
     int st = lr::plan_reserve_batch(plan, S);
@@ -817,12 +824,56 @@ LR_API int lr_response_batched(lr_plan *plan, int64_t S, const int64_t *h_off, c
     P.src.sky = sky;
     P.src.tile_off = plan->d_tile_off;
     P.src.S = S;
+    P.src.gb = gb;
+    P.gen_strain = gb != nullptr;
     P.hp = hp;
     P.hc = hc;
     P.out = xyz;
     P.total_tiles = -1;
     return check_launch(plan->ctx, lr::launch_forward(plan->desc.precision, lr::KIND_FUSED, plan->desc.order, P,
                                                       plan->threads, plan->ctx->sms, stream));
+}
+
+bool gb_finite(const lr_gb &g)
+{
+    return std::isfinite(g.A) && std::isfinite(g.f0) && std::isfinite(g.fdot) && std::isfinite(g.fddot) &&
+           std::isfinite(g.phi0) && std::isfinite(g.iota);
+}
+
+}  // namespace
+
+extern "C" {
+
+LR_API int lr_response_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off,
+                               const double *t0_h, const lr_sky *sky, const double *hp, const double *hc,
+                               double *xyz, void *stream)
+{
+    if (!h_off || !t0_h || !hp || !hc) return LR_ERR_INVALID_ARG;
+    return response_batched_impl(plan, S, h_off, out_off, t0_h, sky, hp, hc, nullptr, xyz, stream);
+}
+
+LR_API int lr_response_gb_batched(lr_plan *plan, int64_t S, const int64_t *out_off, const lr_gb *gb,
+                                  const lr_sky *sky, double *xyz, void *stream)
+{
+    if (!gb) return LR_ERR_INVALID_ARG;
+    return response_batched_impl(plan, S, nullptr, out_off, nullptr, sky, nullptr, nullptr, gb, xyz, stream);
+}
+
+LR_API int lr_response_gb(lr_plan *plan, lr_gb gb, lr_sky sky, double *xyz, void *stream)
+{
+    if (!plan || !xyz) return LR_ERR_INVALID_ARG;
+    if (!gb_finite(gb) || !std::isfinite(sky.lam) || !std::isfinite(sky.beta) || !std::isfinite(sky.psi))
+        return LR_ERR_NONFINITE;
+    lr::FwdParams P = plan->base;
+    P.src.n1 = plan->desc.n;
+    P.src.nh1 = lr::GEN_STRAIN_LEN;
+    P.src.t0h1 = plan->desc.t0;
+    P.src.sky1 = sky;
+    P.src.skyc1 = lr::make_sky(sky);
+    P.src.gb1 = gb;
+    P.gen_strain = 1;
+    P.out = xyz;
+    return launch_single(plan, lr::KIND_FUSED, P, stream);
 }
 
 }  // extern "C"
@@ -899,11 +950,11 @@ int likelihood_single(lr_plan *plan, const double *hp, const double *hc, int64_t
 }
 
 int likelihood_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int64_t *out_off, const double *t0_h,
-                       const lr_sky *sky, const double *hp, const double *hc, const double *data, int64_t n_total,
-                       const double *weights, int logl, double *dh_hh, double *xyz, void *stream)
+                       const lr_sky *sky, const double *hp, const double *hc, const lr_gb *gb, const double *data,
+                       int64_t n_total, const double *weights, int logl, double *dh_hh, double *xyz, void *stream)
 {
-    if (!plan || !h_off || !out_off || !t0_h || !sky || !hp || !hc || !data || !weights || !dh_hh)
-        return LR_ERR_INVALID_ARG;
+    if (!plan || !out_off || !sky || !data || !weights || !dh_hh) return LR_ERR_INVALID_ARG;
+    if (!gb && (!h_off || !t0_h || !hp || !hc)) return LR_ERR_INVALID_ARG;
     if (S < 1 || n_total < 0) return LR_ERR_INVALID_ARG;
     if (S > (int64_t)1 << 24 || n_total > (int64_t)1 << 40) return LR_ERR_RANGE;
     int st = lr::plan_reserve_batch(plan, S);
@@ -922,6 +973,8 @@ int likelihood_batched(lr_plan *plan, int64_t S, const int64_t *h_off, const int
     P.src.sky = sky;
     P.src.tile_off = plan->d_tile_off;
     P.src.S = S;
+    P.src.gb = gb;
+    P.gen_strain = gb != nullptr;
     P.hp = hp;
     P.hc = hc;
     P.out = xyz;
@@ -948,8 +1001,9 @@ LR_API int lr_likelihood_batched(lr_plan *plan, int64_t S, const int64_t *h_off,
                                  const double *data, int64_t n_total, const double *weights, double *dh_hh,
                                  double *xyz, void *stream)
 {
-    return likelihood_batched(plan, S, h_off, out_off, t0_h, sky, hp, hc, data, n_total, weights, 0, dh_hh, xyz,
-                              stream);
+    if (!h_off || !t0_h || !hp || !hc) return LR_ERR_INVALID_ARG;
+    return likelihood_batched(plan, S, h_off, out_off, t0_h, sky, hp, hc, nullptr, data, n_total, weights, 0, dh_hh,
+                              xyz, stream);
 }
 
 LR_API int lr_log_likelihood(lr_plan *plan, const double *hp, const double *hc, int64_t n_h, double t0_h,
@@ -964,8 +1018,18 @@ LR_API int lr_log_likelihood_batched(lr_plan *plan, int64_t S, const int64_t *h_
                                      const double *data, int64_t n_total, const double *weights, double *logl,
                                      double *xyz, void *stream)
 {
-    return likelihood_batched(plan, S, h_off, out_off, t0_h, sky, hp, hc, data, n_total, weights, 1, logl, xyz,
-                              stream);
+    if (!h_off || !t0_h || !hp || !hc) return LR_ERR_INVALID_ARG;
+    return likelihood_batched(plan, S, h_off, out_off, t0_h, sky, hp, hc, nullptr, data, n_total, weights, 1, logl,
+                              xyz, stream);
+}
+
+LR_API int lr_log_likelihood_gb_batched(lr_plan *plan, int64_t S, const int64_t *out_off, const lr_gb *gb,
+                                        const lr_sky *sky, const double *data, int64_t n_total, const double *weights,
+                                        double *logl, double *xyz, void *stream)
+{
+    if (!gb) return LR_ERR_INVALID_ARG;
+    return likelihood_batched(plan, S, nullptr, out_off, nullptr, sky, nullptr, nullptr, gb, data, n_total, weights, 1,
+                              logl, xyz, stream);
 }
 
 LR_API int lr_likelihood_grad(lr_plan *plan, const double *xyz, const double *data, const double *weights,

@@ -75,6 +75,10 @@ struct SrcArgs {
     double t0h1;
     lr_sky sky1;
     SkyConst skyc1;
+    // strain generated on the device (FwdParams::gen_strain): Galactic-binary parameters, device
+    // [S] (batched) or gb1 (single source)
+    const lr_gb *gb;
+    lr_gb gb1;
 };
 
 // Fused likelihood epilogue of the forward launch (Eq. like in the time domain, summed over the
@@ -105,6 +109,8 @@ struct FwdParams {
     int ymax;             // capacity of the staged link window (tile + HL + HR)
     SrcArgs src;
     const double *hp, *hc;  // strain (h+, hx)
+    int gen_strain;         // 1: the strain is a Galactic binary generated on the device (src.gb),
+                            // sampled on the output grid t0 + i dt at every i (no zero extension)
     const double *yin;      // link series input (TDI-only launches)
     double *out;            // y [6][n] or xyz [3][n] (fused likelihood launches: may be null)
     LikeArgs like;
@@ -125,6 +131,10 @@ struct FwdParams {
     const double *cd_w;
     int cd_off[3][2][CHAIN_TERMS];
 };
+
+// generated strain: the source's waveform sampled on the output grid at every index (the
+// strain length used in the window bounds)
+constexpr int64_t GEN_STRAIN_LEN = (int64_t)1 << 62;
 
 // error-word bits
 constexpr int ERR_WINDOW = 1;    // a stencil fell outside its staged window
