@@ -157,7 +157,9 @@ LR_API int lr_plan_tile(const lr_plan *plan, int *tile);
  * Errors: LR_ERR_INVALID_ARG for null pointers. */
 LR_API int lr_valid_range(const lr_plan *plan, int64_t *first, int64_t *last);
 /* Waits for `stream`, then reads and clears the plan's device error word: LR_OK, or
- * LR_ERR_DEVICE / LR_ERR_TIMEOUT if a kernel recorded a fault since the last check. */
+ * LR_ERR_DEVICE / LR_ERR_TIMEOUT if a kernel recorded a fault since the last check, or
+ * LR_ERR_NONFINITE if the only thing recorded is a NaN or infinity in the strain a forward tile
+ * staged or in the likelihood data it read (the outputs it touched are then non-finite too). */
 LR_API int lr_plan_check(lr_plan *plan, void *stream);
 
 /* ------------------------------------------------------------------ forward */

@@ -1,0 +1,484 @@
+// Mixed-precision adjoint kernels (the transposes of the TDI and projection operators for plans
+// of precision LR_MIXED): float-float Lagrange weights and float-float accumulation of float-float
+// cotangents on the FP32 pipe, while the orbit splines, the delays and the read positions stay FP64 and every
+// index split is exact integer work on 64-bit fixed point (44 fractional bits).
+//
+// Structure as the FP64 kernels (lr_bwd.cu): deterministic gathers over inverted tap windows.
+//   KM1  g_y = T^T g_xyz   tile of 256 link samples; per window output the six link delays in fixed
+//                          point, then per chain the chained delays by integer adds, each term's
+//                          weights (float-float, from the exact fraction) and the gather onto every
+//                          link sample of the tile.
+//   KM2  g_h = P^T g_y     tile of 128 strain samples; per window link sample the FP64 geometry,
+//                          the 9 read positions in fixed point and the 18 coefficients as float-
+//                          float, then per read the float-float weights and the gather onto every
+//                          strain sample.
+// Each tile's cotangents are scaled by a power of two (exactly) so that FP32 neither overflows nor
+// underflows; the results are unscaled exactly.
+//
+// Accuracy: the weights are float-float (~2^-45 relative), not FP32: with a static constellation
+// or constant delays every read of a term has the same fraction, and FP32 weight roundings would
+// act as one fixed filter error that a smooth part of the cotangent (the signal mismatch of a
+// residual) sees without the cancellation of the transposed operators; the sky-angle gradient, a
+// sum that cancels strongly, then moved by ~1e-6.  The sky-angle gradient of a mixed plan runs in
+// the FP64 kernel on this g_y.
+#include <cuda_runtime.h>
+
+#include <climits>
+
+#include "lr_bwd.h"
+#include "lr_device.cuh"
+#include "lr_mixed.cuh"
+#include "lr_tdi_table.cuh"
+
+namespace lr {
+namespace {
+
+__constant__ TdiTab c_tdibm = make_tdi_tab();
+constexpr int NTERM_BW = 42;  // 3 channels x 2 chains x 7 delayed terms
+
+// float-float reciprocals 1/d, d = 1 .. 64 (hi the FP32 rounding, lo the rounded remainder)
+struct RecipTab {
+    float hi[65], lo[65];
+};
+constexpr RecipTab make_recip_tab()
+{
+    RecipTab t{};
+    for (int d = 1; d <= 64; ++d) {
+        const double r = 1.0 / (double)d;
+        t.hi[d] = (float)r;
+        t.lo[d] = (float)(r - (double)(float)r);
+    }
+    return t;
+}
+__constant__ RecipTab c_recip = make_recip_tab();
+
+// centered Lagrange weights in float-float: every factor (eps + h - a)/(a + 1) formed exactly up to
+// the float-float product with the reciprocal of (a + 1); prefix products written out, then each
+// multiplied by the suffix product and signed (~2^-45 relative per step)
+template <int T>
+__device__ __forceinline__ void lagrange_w_ff(ff e, float *whi, float *wlo, int stride)
+{
+    constexpr int h = (T - 2) / 2;
+    ff L = {1.0f, 0.0f};
+#pragma unroll 1
+    for (int a = 0; a < T; ++a) {
+        whi[a * stride] = L.hi;
+        wlo[a * stride] = L.lo;
+        L = ff_mul(L, ff_mul(ff_add_f(e, (float)(h - a)), ff{c_recip.hi[a + 1], c_recip.lo[a + 1]}));
+    }
+    ff R = {1.0f, 0.0f};
+#pragma unroll 1
+    for (int a = T - 1; a >= 0; --a) {
+        const ff v = ff_mul(ff{whi[a * stride], wlo[a * stride]}, R);
+        const bool neg = (T - 1 - a) & 1;
+        whi[a * stride] = neg ? -v.hi : v.hi;
+        wlo[a * stride] = neg ? -v.lo : v.lo;
+        R = ff_mul(R, ff_mul(ff_add_f(e, (float)(h - a)), ff{c_recip.hi[T - a], c_recip.lo[T - a]}));
+    }
+}
+
+__device__ __forceinline__ unsigned long long abs_bits64(double v)
+{
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+
+// exponent se putting the largest |value| (bit pattern mb) in [1/2, 1); 0 for zero or non-finite
+__device__ __forceinline__ int scale_exp(unsigned long long mb)
+{
+    const int eb = (int)((mb >> 52) & 0x7ffull);
+    return eb >= 1 && eb <= 2044 ? 1022 - eb : 0;
+}
+
+__device__ __forceinline__ ff ff_scaled(double x, double s)
+{
+    const double v = x * s;  // exact (a power of two, no underflow for |x| near the tile max)
+    const float hi = __double2float_rn(v);
+    return {hi, __double2float_rn(v - (double)hi)};
+}
+
+// acc += (w.hi + w.lo) * (g.hi + g.lo) in float-float
+__device__ __forceinline__ void ff_fma_acc2(ff &acc, float whi, float wlo, float ghi, float glo)
+{
+    const float p = whi * ghi;
+    const float pe = fmaf(whi, ghi, -p);
+    const ff s = two_sum(acc.hi, p);
+    acc.hi = s.hi;
+    acc.lo += s.lo + fmaf(whi, glo, fmaf(wlo, ghi, pe));
+}
+
+__device__ __forceinline__ void block_max_u64(unsigned long long *dst, unsigned long long b)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long c = __shfl_xor_sync(0xffffffffu, b, o);
+        b = c > b ? c : b;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(dst, b);
+}
+
+// ---------------------------------------------------------------- KM1: TDI transpose
+// Shared memory: Lf[6][WN] (int64, link delays in fixed point samples), Dq[WN] (int64, running
+// chained delay of the current chain), Ghi, Glo [3][WN] (float), Whi, Wlo [T][WN] (float-float
+// weights: with constant delays every output of a term reads with the same fraction, and FP32
+// weight roundings would then act as one fixed filter error that a smooth cotangent sees without
+// the TDI cancellation), Mo[WN] (int).
+template <int T>
+__global__ void __launch_bounds__(256, 2) k_tdi_adj_mx(FwdParams P, BwdParams B)
+{
+    constexpr int h = (T - 2) / 2;
+    extern __shared__ __align__(16) long long smi[];
+    const int WN = B.wn;
+    long long *Lf = smi, *Dq = smi + 6 * WN;
+    float *Ghi = reinterpret_cast<float *>(smi + 7 * WN), *Glo = Ghi + 3 * WN, *Whi = Glo + 3 * WN;
+    float *Wlo = Whi + T * WN;
+    int *Mo = reinterpret_cast<int *>(Wlo + T * WN);
+    __shared__ TileInfo ti;
+    __shared__ int mo_lo, mo_hi;
+    __shared__ unsigned long long gmax;
+    __shared__ long long dnest[NTERM_BW];
+    const int64_t total = P.total_tiles >= 0 ? P.total_tiles : P.src.tile_off[P.src.S];
+    for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+        if (threadIdx.x == 0) {
+            ti = tile_info(P, g, 3);
+            if (!ti.ok) atomicOr(P.err, ERR_OFFSETS);
+            gmax = 0ull;
+        }
+        __syncthreads();
+        if (!ti.ok || ti.nb <= 0) {
+            __syncthreads();
+            continue;
+        }
+        const int64_t N = ti.N, k0 = ti.n0, n_lo = k0 - h - 2;
+        const int nb = (int)ti.nb, wn = nb + 2 * h + 5 + B.dmax;
+        const double *gx = B.g_xyz + (ti.out - P.out);
+        // link delays of every window output in fixed point; the largest |g| of the window
+        unsigned long long mb = 0ull;
+        for (int j = threadIdx.x; j < wn; j += blockDim.x) {
+            const int64_t n = n_lo + j;
+            const bool in = n >= 0 && n < N;
+            for (int c = 0; c < 3; ++c) mb = max(mb, in ? abs_bits64(__ldg(gx + c * N + n)) : 0ull);
+            double L[6];
+            orbit_delays(P.to, P.t0 + (double)n * P.dt, L);
+            for (int l = 0; l < 6; ++l) Lf[l * WN + j] = __double2ll_rn(L[l] * P.inv_dt * FX_ONE);
+        }
+        // nested chained delays: per term the nested minus summed delay at the tile centre (it
+        // changes by < 1e-10 samples over a tile), from the plan's knot table
+        if (P.nest_tab && threadIdx.x < NTERM_BW) {
+            const double u = (P.t0 + (double)(k0 + nb / 2) * P.dt - P.nest_t0) * P.nest_inv_dk;
+            const int kk = u <= 0.0 ? 0 : (u >= (double)(P.nest_n - 2) ? P.nest_n - 2 : (int)u);
+            const double f = fmin(fmax(u - (double)kk, 0.0), 1.0);
+            const double a = __ldg(P.nest_tab + kk * NTERM_BW + threadIdx.x);
+            const double b = __ldg(P.nest_tab + (kk + 1) * NTERM_BW + threadIdx.x);
+            dnest[threadIdx.x] = llrint(fma(f, b - a, a) * FX_ONE);
+        }
+        block_max_u64(&gmax, mb);
+        __syncthreads();
+        const int se = scale_exp(gmax);
+        const double up = exp2((double)se), down = exp2((double)-se);
+        for (int j = threadIdx.x; j < wn; j += blockDim.x) {
+            const int64_t n = n_lo + j;
+            const bool in = n >= 0 && n < N;
+            for (int c = 0; c < 3; ++c) {
+                const ff v = in ? ff_scaled(__ldg(gx + c * N + n), up) : ff{0.0f, 0.0f};
+                Ghi[c * WN + j] = v.hi;
+                Glo[c * WN + j] = v.lo;
+            }
+        }
+        ff acc[6];
+#pragma unroll
+        for (int l = 0; l < 6; ++l) acc[l] = {0.0f, 0.0f};
+        const int me = threadIdx.x;
+        const int64_t k = k0 + me;
+        __syncthreads();
+        if (me < nb) {
+            const int jk = (int)(k - n_lo);
+            for (int ch = 0; ch < 3; ++ch) {
+                const ff gv = {Ghi[ch * WN + jk], Glo[ch * WN + jk]};
+#pragma unroll
+                for (int l = 0; l < 6; ++l) {
+                    if (l == c_tdibm.link[ch][0][0]) acc[l] = ff_add(acc[l], gv);
+                    if (l == c_tdibm.link[ch][1][0]) acc[l] = ff_sub(acc[l], gv);
+                }
+            }
+        }
+        for (int ch = 0; ch < 3; ++ch)
+            for (int c = 0; c < 2; ++c) {
+                for (int j = threadIdx.x; j < wn; j += blockDim.x) Dq[j] = 0;
+                for (int q = 1; q <= P.q_terms; ++q) {
+                    if (threadIdx.x == 0) {
+                        mo_lo = INT_MAX;
+                        mo_hi = INT_MIN;
+                    }
+                    __syncthreads();
+                    const int pl = c_tdibm.pair[ch][c][q];
+                    const long long dn = P.nest_tab ? dnest[(ch * 2 + c) * 7 + q - 1] : 0ll;
+                    int lmin = INT_MAX, lmax = INT_MIN;
+                    for (int j = threadIdx.x; j < wn; j += blockDim.x) {
+                        const long long D = Dq[j] + Lf[pl * WN + j];
+                        Dq[j] = D;
+                        const Split s = split_fx(-(D + dn));  // read at n - D: index n + m
+                        Mo[j] = s.m;
+                        lmin = min(lmin, s.m);
+                        lmax = max(lmax, s.m);
+                        lagrange_w_ff<T>(ff{s.ehi, s.elo}, Whi + j, Wlo + j, WN);
+                    }
+                    atomicMin(&mo_lo, lmin);
+                    atomicMax(&mo_hi, lmax);
+                    __syncthreads();
+                    if (me < nb) {
+                        // outputs n whose stencil [n + Mo - h, n + Mo + h + 1] contains k
+                        int jlo = (int)(k - h - 1 - mo_hi - n_lo), jhi = (int)(k + h - mo_lo - n_lo);
+                        jlo = max(jlo, 0);
+                        jhi = min(jhi, wn - 1);
+                        ff s = {0.0f, 0.0f};
+                        for (int j = jlo; j <= jhi; ++j) {
+                            const int a = (int)(k - (n_lo + j + Mo[j])) + h;
+                            if (a >= 0 && a < T)
+                                ff_fma_acc2(s, Whi[a * WN + j], Wlo[a * WN + j], Ghi[ch * WN + j], Glo[ch * WN + j]);
+                        }
+                        const int lk = c_tdibm.link[ch][c][q];
+#pragma unroll
+                        for (int l = 0; l < 6; ++l)
+                            if (l == lk) acc[l] = c == 0 ? ff_add(acc[l], s) : ff_sub(acc[l], s);
+                    }
+                    __syncthreads();
+                }
+            }
+        if (me < nb) {
+            double *gy = B.g_y + 6 * (ti.out - P.out) / 3;
+#pragma unroll
+            for (int l = 0; l < 6; ++l) gy[l * N + k] = ((double)acc[l].hi + (double)acc[l].lo) * down;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- KM2: projection transpose
+struct LinkGeoM {
+    double xp, xc, den;
+};
+
+__device__ __forceinline__ LinkGeoM link_geo_m(const SkyConst &S, const double *x, int l)
+{
+    const int LR[6] = {0, 1, 2, 0, 2, 1}, LS[6] = {1, 2, 0, 2, 1, 0};
+    const int r = LR[l], s = LS[l];
+    double d0 = x[3 * r] - x[3 * s], d1 = x[3 * r + 1] - x[3 * s + 1], d2 = x[3 * r + 2] - x[3 * s + 2];
+    const double inv = rsqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    d0 *= inv;
+    d1 *= inv;
+    d2 *= inv;
+    const double un = S.u[0] * d0 + S.u[1] * d1 + S.u[2] * d2;
+    const double vn = S.v[0] * d0 + S.v[1] * d1 + S.v[2] * d2;
+    const double kn = S.k[0] * d0 + S.k[1] * d1 + S.k[2] * d2;
+    const double xip = un * un - vn * vn, xic = 2.0 * un * vn;
+    return {S.c2p * xip + S.s2p * xic, -S.s2p * xip + S.c2p * xic, 0.5 / (1.0 - kn)};
+}
+
+// Shared memory: X[9][WK] (int64, read positions relative to the link sample, fixed point),
+// CF[18][WK] (double, then float-float pairs in place), Whi, Wlo [T][WK] (float-float weights:
+// with a static constellation every sample of a read has the same fraction, as in the TDI
+// transpose), Mo[WK] (int).
+template <int T>
+__global__ void __launch_bounds__(256, 2) k_proj_adj_mx(FwdParams P, BwdParams B)
+{
+    constexpr int h = (T - 2) / 2;
+    extern __shared__ __align__(16) long long smi[];
+    const int WK = B.wk;
+    long long *X = smi;
+    double *CF = reinterpret_cast<double *>(smi + 9 * WK);
+    float *Whi = reinterpret_cast<float *>(smi + 27 * WK), *Wlo = Whi + T * WK;
+    int *Mo = reinterpret_cast<int *>(Wlo + T * WK);
+    __shared__ TileInfo ti;
+    __shared__ SkyConst skc;
+    __shared__ int64_t i0s, k_lo_s;
+    __shared__ int nbs, wks, mo_lo, mo_hi;
+    __shared__ double u0s;
+    __shared__ unsigned long long cmax;
+    const int64_t total = B.h_total_tiles >= 0 ? B.h_total_tiles : B.h_tile_off[P.src.S];
+    for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+        if (threadIdx.x == 0) {
+            FwdParams Q = P;
+            Q.src.tile_off = B.h_tile_off;
+            Q.tile = B.tile_h;
+            ti = tile_info(Q, g, 3);
+            if (!ti.ok) atomicOr(P.err, ERR_OFFSETS);
+            skc = make_sky(ti.sky);
+            u0s = (P.t0 - ti.t0h) / P.dt;
+            cmax = 0ull;
+        }
+        __syncthreads();
+        if (!ti.ok) {
+            __syncthreads();
+            continue;
+        }
+        if (threadIdx.x == 0) {
+            // the strain tile [i0, i0 + nb) and the window of link samples whose reads reach it
+            // (the same bounds as the FP64 kernel)
+            const int64_t i0 = ti.n0;
+            const int64_t nbh = ti.nh - i0;
+            nbs = (int)(nbh < B.tile_h ? (nbh > 0 ? nbh : 0) : B.tile_h);
+            i0s = i0;
+            const int64_t k_ref = i0 - (int64_t)floor(u0s);
+            double x[9], L[6];
+            orbit_all(P.po, P.t0 + (double)k_ref * P.dt, x, L);
+            double umin = 1e300, umax = -1e300;
+            for (int rd = 0; rd < 9; ++rd) {
+                const int sc = rd < 3 ? rd : (rd == 3 ? 1 : rd == 4 ? 2 : rd == 5 ? 0 : rd == 6 ? 2 : rd == 7 ? 1 : 0);
+                double u = u0s - (skc.k[0] * x[3 * sc] + skc.k[1] * x[3 * sc + 1] + skc.k[2] * x[3 * sc + 2]) /
+                                     C_LIGHT * P.inv_dt;
+                if (rd >= 3) u -= L[rd - 3] * P.inv_dt;
+                umin = fmin(umin, u);
+                umax = fmax(umax, u);
+            }
+            k_lo_s = i0 - h - 2 - (int64_t)ceil(umax) - B.kmargin;
+            const int64_t k_hi = i0 + nbs + h + 1 - (int64_t)floor(umin) + B.kmargin;
+            int64_t w = k_hi - k_lo_s;
+            if (w > WK) {
+                atomicOr(P.err, ERR_WINDOW);
+                w = WK;
+            }
+            wks = (int)w;
+        }
+        __syncthreads();
+        const int nb = nbs, wk = wks;
+        const int64_t k_lo = k_lo_s, i0 = i0s, N = ti.N;
+        if (nb <= 0) {
+            __syncthreads();
+            continue;
+        }
+        const double *gy = B.g_y + 6 * (ti.out - P.out) / 3;
+        // per window link sample: read positions (fixed point, relative to k) and coefficients
+        unsigned long long mb = 0ull;
+        for (int j = threadIdx.x; j < wk; j += blockDim.x) {
+            const int64_t k = k_lo + j;
+            if (k < 0 || k >= N) {
+                for (int rd = 0; rd < 9; ++rd) {
+                    X[rd * WK + j] = __double2ll_rn(u0s * FX_ONE);
+                    CF[(2 * rd) * WK + j] = 0.0;
+                    CF[(2 * rd + 1) * WK + j] = 0.0;
+                }
+                continue;
+            }
+            double x[9], L[6];
+            orbit_all(P.po, P.t0 + (double)k * P.dt, x, L);
+            double sig[3];
+            for (int i = 0; i < 3; ++i)
+                sig[i] = (skc.k[0] * x[3 * i] + skc.k[1] * x[3 * i + 1] + skc.k[2] * x[3 * i + 2]) / C_LIGHT * P.inv_dt;
+            double rp[3] = {0.0, 0.0, 0.0}, rc[3] = {0.0, 0.0, 0.0};
+            for (int l = 0; l < 6; ++l) {
+                const int LR[6] = {0, 1, 2, 0, 2, 1}, LS[6] = {1, 2, 0, 2, 1, 0};
+                const LinkGeoM q = link_geo_m(skc, x, l);
+                const double gl = __ldg(gy + l * N + k) * q.den;
+                X[(3 + l) * WK + j] = __double2ll_rn((u0s - L[l] * P.inv_dt - sig[LS[l]]) * FX_ONE);
+                const double cp = gl * q.xp, cc = gl * q.xc;
+                CF[(2 * (3 + l)) * WK + j] = cp;
+                CF[(2 * (3 + l) + 1) * WK + j] = cc;
+                mb = max(mb, max(abs_bits64(cp), abs_bits64(cc)));
+                rp[LR[l]] -= cp;
+                rc[LR[l]] -= cc;
+            }
+            for (int r = 0; r < 3; ++r) {
+                X[r * WK + j] = __double2ll_rn((u0s - sig[r]) * FX_ONE);
+                CF[(2 * r) * WK + j] = rp[r];
+                CF[(2 * r + 1) * WK + j] = rc[r];
+                mb = max(mb, max(abs_bits64(rp[r]), abs_bits64(rc[r])));
+            }
+        }
+        block_max_u64(&cmax, mb);
+        __syncthreads();
+        const int se = scale_exp(cmax);
+        const double up = exp2((double)se), down = exp2((double)-se);
+        // coefficients to scaled float-float pairs, in place (each thread its own 8-byte slots)
+        for (int t = threadIdx.x; t < 18 * wk; t += blockDim.x) {
+            const int r = t / wk, j = t - r * wk;
+            const ff v = ff_scaled(CF[r * WK + j], up);
+            reinterpret_cast<float2 *>(CF)[r * WK + j] = make_float2(v.hi, v.lo);
+        }
+        __syncthreads();
+        const float2 *CFf = reinterpret_cast<const float2 *>(CF);
+        const int me = threadIdx.x;
+        const int64_t i = i0 + me;
+        ff ap = {0.0f, 0.0f}, ac = {0.0f, 0.0f};
+        for (int rd = 0; rd < 9; ++rd) {
+            if (threadIdx.x == 0) {
+                mo_lo = INT_MAX;
+                mo_hi = INT_MIN;
+            }
+            __syncthreads();
+            int lmin = INT_MAX, lmax = INT_MIN;
+            for (int j = threadIdx.x; j < wk; j += blockDim.x) {
+                const Split s = split_fx(X[rd * WK + j]);
+                Mo[j] = s.m;
+                lmin = min(lmin, s.m);
+                lmax = max(lmax, s.m);
+                lagrange_w_ff<T>(ff{s.ehi, s.elo}, Whi + j, Wlo + j, WK);
+            }
+            atomicMin(&mo_lo, lmin);
+            atomicMax(&mo_hi, lmax);
+            __syncthreads();
+            if (me < nb) {
+                // link samples k whose read stencil [k + Mo - h, k + Mo + h + 1] contains i
+                int jlo = (int)(i - h - 1 - mo_hi - k_lo), jhi = (int)(i + h - mo_lo - k_lo);
+                jlo = max(jlo, 0);
+                jhi = min(jhi, wk - 1);
+                for (int j = jlo; j <= jhi; ++j) {
+                    const int a = (int)(i - (k_lo + j + Mo[j])) + h;
+                    if (a >= 0 && a < T) {
+                        const float wh = Whi[a * WK + j], wl = Wlo[a * WK + j];
+                        const float2 cp = CFf[(2 * rd) * WK + j], cc = CFf[(2 * rd + 1) * WK + j];
+                        ff_fma_acc2(ap, wh, wl, cp.x, cp.y);
+                        ff_fma_acc2(ac, wh, wl, cc.x, cc.y);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (me < nb) {
+            B.g_hp[(ti.hp - P.hp) + i] = ((double)ap.hi + (double)ap.lo) * down;
+            B.g_hc[(ti.hp - P.hp) + i] = ((double)ac.hi + (double)ac.lo) * down;
+        }
+        __syncthreads();
+    }
+}
+
+#define LR_BM_ORDERS(X) X(1) X(3) X(5) X(7) X(9) X(11) X(13) X(15) X(17) X(19) X(21) X(23) X(25) X(31) X(41)
+
+void *bwd_kernel_mx(int kind, int order)
+{
+    switch (order) {
+#define LR_CASE(p) \
+    case p: return kind == 0 ? (void *)k_tdi_adj_mx<p + 1> : (void *)k_proj_adj_mx<p + 1>;
+        LR_BM_ORDERS(LR_CASE)
+#undef LR_CASE
+        default: return nullptr;
+    }
+}
+
+}  // namespace
+
+size_t smem_bwd_mx(int kind, int order, const BwdParams &B)
+{
+    const size_t T = (size_t)order + 1;
+    return kind == 0 ? (size_t)B.wn * (7 * 8 + 6 * 4 + 2 * T * 4 + 4) : (size_t)B.wk * (27 * 8 + 2 * T * 4 + 4);
+}
+
+int launch_bwd_mx(int kind, int order, const FwdParams &P, const BwdParams &B, int sms, void *stream)
+{
+    void *k = bwd_kernel_mx(kind, order);
+    if (!k) return (int)cudaErrorInvalidValue;
+    const size_t smem = smem_bwd_mx(kind, order, B);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem);
+    if (e != cudaSuccess) return (int)e;
+    if (per_sm < 1) return (int)cudaErrorLaunchOutOfResources;
+    int64_t grid = (int64_t)per_sm * sms;
+    const int64_t known = kind == 1 ? B.h_total_tiles : P.total_tiles;
+    if (known >= 0 && known < grid) grid = known;
+    if (grid < 1) grid = 1;
+    void *args[] = {(void *)&P, (void *)&B};
+    return (int)cudaLaunchKernel(k, dim3((unsigned)grid), dim3(256), args, smem, (cudaStream_t)stream);
+}
+
+}  // namespace lr

@@ -142,6 +142,19 @@ __device__ inline void stage(double *dst, const double *src, int64_t lo, int len
     }
 }
 
+// stage() of the strain, recording a NaN or infinity in the error word
+__device__ inline void stage_checked(double *dst, const double *src, int64_t lo, int len, int64_t n_src, int *err)
+{
+    bool bad = false;
+    for (int j = threadIdx.x; j < len; j += blockDim.x) {
+        int64_t i = lo + j;
+        const double v = (i >= 0 && i < n_src) ? __ldg(src + i) : 0.0;
+        dst[j] = v;
+        bad |= !isfinite(v);
+    }
+    if (bad) atomicOr(err, ERR_NONFINITE);
+}
+
 // the strain window of a tile: staged from the caller's arrays, or generated (Galactic binary on
 // the output grid, strain index = output index)
 __device__ inline void stage_strain(const FwdParams &P, const TileInfo &ti, double *hwp, double *hwc, int64_t lo,
@@ -150,8 +163,8 @@ __device__ inline void stage_strain(const FwdParams &P, const TileInfo &ti, doub
     if (P.gen_strain) {
         for (int j = threadIdx.x; j < len; j += blockDim.x) gb_strain(ti.gb, P.t0, P.dt, lo + j, hwp[j], hwc[j]);
     } else {
-        stage(hwp, ti.hp, lo, len, ti.nh);
-        stage(hwc, ti.hc, lo, len, ti.nh);
+        stage_checked(hwp, ti.hp, lo, len, ti.nh, P.err);
+        stage_checked(hwc, ti.hc, lo, len, ti.nh, P.err);
     }
 }
 
@@ -205,9 +218,11 @@ __global__ void __launch_bounds__(256) k_fused64(FwdParams P)
 #pragma unroll
                     for (int c = 0; c < 3; ++c) ti.out[c * ti.N + n] = o[c];
                 }
-                if (like && ti.dat)
-                    like_terms(P.like, o[0], o[1], o[2], __ldg(ti.dat + n), __ldg(ti.dat + ti.N + n),
-                               __ldg(ti.dat + 2 * ti.N + n), dh, hh);
+                if (like && ti.dat) {
+                    const double da = __ldg(ti.dat + n), de = __ldg(ti.dat + ti.N + n), dT = __ldg(ti.dat + 2 * ti.N + n);
+                    if (!(isfinite(da) && isfinite(de) && isfinite(dT))) atomicOr(P.err, ERR_NONFINITE);
+                    like_terms(P.like, o[0], o[1], o[2], da, de, dT, dh, hh);
+                }
             }
             if (like) {
                 block_sum2(dh, hh, red);

@@ -1245,7 +1245,11 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
         // ---- scaled float-float values
         {
             const int se = tile_scale_exp(ts.maxbits);
-            if (tid == 0) sh.unscale_e = -se;
+            if (tid == 0) {
+                sh.unscale_e = -se;
+                // a NaN or infinity orders above every finite bit pattern
+                if (ts.maxbits >= 0x7ff0000000000000ull) atomicOr(P.err, ERR_NONFINITE);
+            }
             if (KIND != KIND_TDI) {
                 for (int j = tid; j < wlen; j += blockDim.x) {
                     const ff a = ff_from_double_scaled(pf[j], se), b = ff_from_double_scaled(pf[MX_WCAP + j], se);
@@ -1382,11 +1386,15 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
                 const int se = -sh.unscale_e;
                 const float *xs = smf + OFF_XYZ;
                 float dh = 0.0f, hh = 0.0f;
+                bool bad = false;
                 if (ts.ti.dat)
-                    for (int i = tid; i < nb; i += blockDim.x)
+                    for (int i = tid; i < nb; i += blockDim.x) {
+                        bad |= !(isfinite(ld[i]) && isfinite(ld[XYZ_CAP + i]) && isfinite(ld[2 * XYZ_CAP + i]));
                         like_terms_f(P.like, xs[i], xs[XYZ_CAP + i], xs[2 * XYZ_CAP + i],
                                      ff_from_double_scaled(ld[i], se).hi, ff_from_double_scaled(ld[XYZ_CAP + i], se).hi,
                                      ff_from_double_scaled(ld[2 * XYZ_CAP + i], se).hi, dh, hh);
+                    }
+                if (bad) atomicOr(P.err, ERR_NONFINITE);
                 block_sum2f(dh, hh, sh.redf);
                 // undo the scale 2^se of both factors (exactly, by integer work); the weight
                 // normalisation is undone once per source by the reduction

@@ -673,6 +673,7 @@ LR_API int lr_plan_check(lr_plan *plan, void *stream)
         if (e != cudaSuccess) return cuda_fail(plan->ctx, e);
     }
     if (flag & lr::ERR_TIMEOUT) return LR_ERR_TIMEOUT;
+    if (flag == lr::ERR_NONFINITE) return LR_ERR_NONFINITE;
     if (flag) return LR_ERR_DEVICE;
     return LR_OK;
 }
@@ -722,9 +723,11 @@ int backward_launch(lr_plan *plan, lr::FwdParams &P, lr::BwdParams &B, int64_t S
 {
     const int sms = plan->ctx->sms;
     const int order = plan->desc.order;
-    int e = lr::launch_bwd(0, order, P, B, sms, stream);
+    // mixed plans: the TDI and projection transposes in mixed precision, the sky gradient in FP64
+    const bool mx = plan->desc.precision == LR_MIXED;
+    int e = mx ? lr::launch_bwd_mx(0, order, P, B, sms, stream) : lr::launch_bwd(0, order, P, B, sms, stream);
     if (!e && g_sky) e = lr::launch_bwd(2, order, P, B, sms, stream);
-    if (!e) e = lr::launch_bwd(1, order, P, B, sms, stream);
+    if (!e) e = mx ? lr::launch_bwd_mx(1, order, P, B, sms, stream) : lr::launch_bwd(1, order, P, B, sms, stream);
     if (!e && g_sky) e = lr::launch_sky_reduce(B.partial, ktile_off, S, P.total_tiles, g_sky, stream);
     return check_launch(plan->ctx, e);
 }

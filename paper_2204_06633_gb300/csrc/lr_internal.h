@@ -140,6 +140,7 @@ constexpr int64_t GEN_STRAIN_LEN = (int64_t)1 << 62;
 constexpr int ERR_WINDOW = 1;    // a stencil fell outside its staged window
 constexpr int ERR_OFFSETS = 2;   // batched offsets not monotone
 constexpr int ERR_TIMEOUT = 4;   // bounded wait ran out
+constexpr int ERR_NONFINITE = 8; // a NaN or infinity in the strain or likelihood data a tile read
 
 }  // namespace lr
 

@@ -1,9 +1,12 @@
 """Mixed-precision batched forward + backward at full size: 256 one-year sources (N = 3 153 600
 each, parameters drawn as for the batched workload, seed 5), flexing orbit, order 41, in the
 launch configuration of the batched calls.  Forward: every source's X, Y, Z at sampled outputs
-against the oracle (relative L2 <= 1e-6 per source).  Backward (the adjoint runs in FP64 for
-both plan precisions): the batched dot-product identity <R h, g> = <h, R^T g> with the mixed
-forward, which holds at any size to the forward's own accuracy.  Device memory: about 105 GB."""
+against the oracle (relative L2 <= 1e-6 per source).  Backward (the mixed adjoint: FP32 taps
+and float-float sums in the transposes, the sky gradient in FP64): the batched dot-product identity <R h, g> = <h, R^T g> with the mixed
+forward, which holds at any size to the forward's own accuracy, and per source the gradients of
+a cotangent on a window of 4000 outputs (zero elsewhere) against the oracle's gradients of the same
+cotangent on a sub-span around the window (the gradients of such a cotangent vanish outside the
+window's reach, so the sub-span result is exact).  Device memory: about 105 GB."""
 import time
 
 import numpy as np
@@ -90,6 +93,41 @@ def test_config5_mixed_forward_and_backward():
     norm = (dot(xyz, xyz) * dot(g, g)) ** 0.5
     assert abs(lhs - rhs) <= 1e-6 * norm
     assert torch.isfinite(g_sky).all()
+    del g_hp, g_hc, g_sky
+    # per-source gradients against the oracle: white cotangents on a window of W outputs
+    W, H = 4000, 200
+    pick = rng.choice(S, 4, replace=False)
+    gw = torch.zeros(3 * S * N, dtype=torch.float64, device=dev)
+    win = {}
+    for s in pick:
+        a0 = int(rng.integers(H + 1000, N - W - H - 1000))
+        vals = rng.normal(size=(3, W))
+        win[s] = (a0, vals)
+        for c in range(3):
+            gw[(3 * s + c) * N + a0:(3 * s + c) * N + a0 + W] = torch.from_numpy(vals[c])
+    g_hp, g_hc, g_sky = plan.backward_batched(*args, d_hp, d_hc, gw)
+    plan.check()
+    g_sky = g_sky.cpu().numpy()
+    worst_h = worst_s = 0.0
+    for s in pick:
+        a0, vals = win[s]
+        src = srcs[s]
+        lo, n_sub = a0 - H, W + 2 * H
+        a, b = strain[s]
+        gsub = np.zeros((3, n_sub))
+        gsub[:, H:H + W] = vals
+        rp, rc, rs, scale = oracle.backward(P, 2, DT, T0 + lo * DT, n_sub, orc, orc, a[lo:lo + n_sub + 2 * m],
+                                            b[lo:lo + n_sub + 2 * m], t0h[s] + lo * DT, src.lam, src.beta, src.psi,
+                                            gsub, with_scale=True)
+        gp = g_hp[s * nh + lo:s * nh + lo + n_sub + 2 * m].cpu().numpy()
+        gc = g_hc[s * nh + lo:s * nh + lo + n_sub + 2 * m].cpu().numpy()
+        eh = np.linalg.norm(np.r_[gp - rp, gc - rc]) / np.linalg.norm(np.r_[rp, rc])
+        assert eh <= 1e-6, f"source {s}: strain gradient rel L2 {eh:.2e}"
+        bound = np.maximum(1e-6 * np.abs(rs), 4 * (P + 17) * 2.0 ** -24 * scale)
+        assert np.all(np.abs(g_sky[s] - rs) <= bound), (s, g_sky[s], rs, bound)
+        worst_h = max(worst_h, eh)
+        worst_s = max(worst_s, float(np.max(np.abs(g_sky[s] - rs) / np.abs(rs))))
     print(f"config 5: forward (mixed) {t_fwd:.2f} s = {6 * S * N / t_fwd:.3e} link-samples/s, worst sampled "
-          f"rel L2 {worst:.2e}; backward (FP64 adjoint) {t_bwd:.2f} s; adjoint identity "
-          f"{abs(lhs - rhs) / norm:.1e} of |Rh||g|")
+          f"rel L2 {worst:.2e}; backward (mixed adjoint) {t_bwd:.2f} s; adjoint identity "
+          f"{abs(lhs - rhs) / norm:.1e} of |Rh||g|; per-source gradients against the oracle (window of {W} "
+          f"outputs): strain rel L2 <= {worst_h:.2e}, sky angles rel <= {worst_s:.2e}")

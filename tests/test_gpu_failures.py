@@ -104,3 +104,28 @@ def test_device_detected_fault_is_reported(ctx, orbit):
         plan.check()
     assert e.value.status == DEVICE
     plan.check()  # cleared
+
+
+@pytest.mark.parametrize("precision", [lr.FP64, lr.MIXED])
+def test_nonfinite_strain_and_data_are_reported(ctx, orbit, precision):
+    """A NaN in the strain or an infinity in the likelihood data: the kernels record it and
+    lr_plan_check reports LR_ERR_NONFINITE (then clears it); finite inputs stay silent."""
+    N, p = 5000, 11
+    src = synth.draw_sources(1, seed=4, A=1e-21)[0]
+    t0h, hp, hc = synth.gb_input(src, 0.0, DT, N, p)
+    plan = lr.Plan(ctx, p, N, DT, orbit, precision=precision)
+    d = lambda a: torch.tensor(a, device="cuda:0")  # noqa: E731
+    sky = (src.lam, src.beta, src.psi)
+    plan.response(d(hp), d(hc), t0h, sky)
+    plan.check()
+    bad = hp.copy()
+    bad[N // 2] = np.nan
+    plan.response(d(bad), d(hc), t0h, sky)
+    assert status_of(plan.check) == NONFINITE
+    plan.check()  # cleared
+    data = np.zeros((3, N))
+    plan.likelihood(d(hp), d(hc), t0h, sky, d(data))
+    plan.check()
+    data[1, 17] = np.inf
+    plan.likelihood(d(hp), d(hc), t0h, sky, d(data))
+    assert status_of(plan.check) == NONFINITE
