@@ -428,6 +428,11 @@ def run_ours(args):
     split = None
     if rank == 0 and not args.no_split:
         split = split_times(lr, ctx, p, dev, stream)
+    c5 = None
+    if rank == 0 and args.config5:
+        del d_hp, d_hc, d_xyz
+        torch.cuda.empty_cache()
+        c5 = config5_times(lr, ctx, dev, stream, args.config5, with_fp64=not args.no_fp64)
 
     if rank != 0:
         return
@@ -460,6 +465,8 @@ def run_ours(args):
             "rel_error_vs_oracle": parity and parity["rel_error_vs_oracle"],
             "error_over_bound": parity and parity["error_over_bound"], "parity": parity, "roofline": roof, "e2e": e2e, "gpu_launches": (3 if precision == lr.MIXED else 2) * args.steps,
             "clocks": clocks, "fp64": fp64, "split": split, "likelihood": like}
+    if c5:
+        line["differentiation"] = c5
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = oracle_rate(lens, srcs, p, orb)
         if args.oracle_configs:
@@ -542,6 +549,60 @@ def split_times(lr, ctx, p, dev, stream, reps=5):
             res[name] = _time_call(lambda: plan.response(d_hp, d_hc, t0h, sky, xyz, stream=stream), stream, reps)
             plan.check(stream)
         out["templates_fused_ms"][tname] = res
+    return out
+
+
+def config5_times(lr, ctx, dev, stream, n_sources=256, with_fp64=True):
+    """The differentiation workload: n_sources one-year sources (N = 3,153,600; parameters drawn
+    as for the batch, seed 5), flexing orbit, order 41: the batched forward and the batched
+    backward (g_h+, g_hx and the sky-angle gradients of white cotangents) per precision, one
+    warm-up and one timed call each (CUDA events).  The strain is generated on the device by the
+    library's Galactic-binary generator (the same polarisations the arrays would hold)."""
+    import torch
+
+    N, p = 3_153_600, 41
+    srcs = synth.draw_sources(n_sources, seed=5, A=1e-22, fdot=1e-17)
+    m = synth.input_margin_samples(DT, p)
+    nh = N + 2 * m
+    S = n_sources
+    h_off = torch.arange(S + 1, dtype=torch.int64, device=dev) * nh
+    out_off = torch.arange(S + 1, dtype=torch.int64, device=dev) * N
+    t0h = torch.full((S,), T0 - m * DT, dtype=torch.float64, device=dev)
+    sky = torch.tensor([[s.lam, s.beta, s.psi] for s in srcs], dtype=torch.float64, device=dev)
+    hp = torch.empty(S * nh, dtype=torch.float64, device=dev)
+    hc = torch.empty(S * nh, dtype=torch.float64, device=dev)
+    for s, src in enumerate(srcs):
+        a, b = lr.gb_polarisations((src.A, src.f, src.fdot, src.fddot_value(), src.phi0, src.iota), T0 - m * DT, DT,
+                                   nh, device=dev, stream=stream)
+        hp[s * nh:(s + 1) * nh] = a
+        hc[s * nh:(s + 1) * nh] = b
+    orb = synth.orbit_flexing(T0 - 3e5, T0 + DT * N + 3e5)
+    o = lr.Orbit(ctx, orb.t_knots, orb.pos, None)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(20220413)
+    g = torch.randn(3 * S * N, dtype=torch.float64, device=dev, generator=gen)
+    out = {"workload": "%d one-year sources (N = 3,153,600), flexing orbit, order 41, white cotangents" % S}
+    for name, prec in (("mixed", lr.MIXED), ("fp64", lr.FP64)):
+        if prec == lr.FP64 and not with_fp64:
+            continue
+        plan = lr.Plan(ctx, p, 1, DT, o, t0=T0, precision=prec)
+        args = (h_off, out_off, t0h, sky, hp, hc)
+        fwd = lambda: plan.response_batched(*args, stream=stream)  # noqa: E731
+        bwd = lambda: plan.backward_batched(*args, g, stream=stream)  # noqa: E731
+        res = {}
+        for k, f in (("forward_s", fwd), ("backward_s", bwd)):
+            f()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = f()
+            b.record(stream)
+            torch.cuda.synchronize()
+            res[k] = a.elapsed_time(b) * 1e-3
+            del r
+        plan.check(stream)
+        res["backward_link_samples_per_s"] = 6 * S * N / res["backward_s"]
+        out[name] = res
     return out
 
 
@@ -639,6 +700,9 @@ def main():
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config5", type=int, default=0, metavar="S",
+                    help="also time the differentiation workload (S one-year sources, order 41) forward and backward "
+                         "in both precisions (S = 256 is the full workload: ~110 GB of device memory)")
     ap.add_argument("--oracle-configs", action="store_true",
                     help="also time the FP64 oracle on configs 1, 2 and 4 in full (about a minute)")
     args = ap.parse_args()

@@ -170,7 +170,7 @@ __device__ inline void stage_strain(const FwdParams &P, const TileInfo &ti, doub
 
 // ---------------------------------------------------------------- kernels
 template <int T>
-__global__ void __launch_bounds__(256) k_fused64(FwdParams P)
+__global__ void __launch_bounds__(256, 2) k_fused64(FwdParams P)
 {
     extern __shared__ double sm[];
     double *hwp = sm, *hwc = sm + P.wmax, *ys = sm + 2 * P.wmax;
