@@ -5,9 +5,10 @@
 //
 // Structure as the FP64 kernels (lr_bwd.cu): deterministic gathers over inverted tap windows.
 //   KM1  g_y = T^T g_xyz   tile of 256 link samples; per window output the six link delays in fixed
-//                          point, then per chain the chained delays by integer adds, each term's
-//                          weights (float-float, from the exact fraction) and the gather onto every
-//                          link sample of the tile.
+//                          point; per term float-float reference weights at the window centre with
+//                          their Taylor coefficients; then per chain the chained delays by integer
+//                          adds and the gather onto every link sample of the tile, each weight the
+//                          reference expanded in the output's (tiny) fraction offset.
 //   KM2  g_h = P^T g_y     tile of 128 strain samples; per window link sample the FP64 geometry,
 //                          the 9 read positions in fixed point and the 18 coefficients as float-
 //                          float, then per read the float-float weights and the gather onto every
@@ -117,11 +118,88 @@ __device__ __forceinline__ void block_max_u64(unsigned long long *dst, unsigned 
 }
 
 // ---------------------------------------------------------------- KM1: TDI transpose
+// Every delayed read of a term at the window's outputs has a fraction within a few 1e-5 of the
+// term's fraction at the window centre (the chained delays drift by ~1e-7 samples per sample), so
+// its weights are the reference weights expanded to third order in the offset Delta:
+//   w_a(eps_ref + Delta) = W0_a + Delta (W1_a + Delta (W2_a + Delta W3_a))
+// with W0 exact in float-float and the derivatives from the product w_a = Q_a N_a: N_a the (at most
+// two) factors eps / (a - h) and (eps - 1) / (a - h - 1) of the nodes next to the read, which can be
+// small, differentiated exactly; Q_a the other factors (|eps + h - i| >= 1), differentiated through
+// the sums S_k = sum 1 / (eps + h - i)^k (S1 in float-float).  The fourth-order term is below
+// 1e-13 for |Delta| <= 5e-5.  Terms whose window crosses an integer sample (a different stencil) or
+// drifts further take exact float-float weights read by read.
+
+__device__ __forceinline__ ff recip_signed(int d)
+{
+    const int m = d < 0 ? -d : d;
+    const ff r = {c_recip.hi[m], c_recip.lo[m]};
+    return d < 0 ? ff_neg(r) : r;
+}
+
+// reference weight and Taylor coefficients of tap a at eps (float-float): out = W0.hi, W0.lo, W1,
+// W2, W3
+template <int T>
+__device__ void ref_weight_taylor(ff e, int a, float *out)
+{
+    constexpr int h = (T - 2) / 2;
+    ff Q = {1.0f, 0.0f}, S1 = {0.0f, 0.0f};
+    float S2 = 0.0f, S3 = 0.0f;
+#pragma unroll 1
+    for (int i = 0; i < T; ++i) {
+        if (i == a || i == h || i == h + 1) continue;
+        const ff x = ff_add_f(e, (float)(h - i));  // exact: |x| >= 1
+        Q = ff_mul(Q, ff_mul(x, recip_signed(a - i)));
+        const float r = 1.0f / x.hi;
+        const float er = fmaf(-x.hi, r, 1.0f) - x.lo * r;
+        const ff rx = fast_two_sum(r, er * r);  // 1/x to ~2^-46
+        S1 = ff_add(S1, rx);
+        const float r2 = rx.hi * rx.hi;
+        S2 += r2;
+        S3 = fmaf(r2, rx.hi, S3);
+    }
+    ff N, N1;
+    float N2 = 0.0f;
+    if (a == h) {  // the factor (eps - 1) / (h - (h + 1)) = 1 - eps
+        N = ff_add_f(ff_neg(e), 1.0f);
+        N1 = {-1.0f, 0.0f};
+    } else if (a == h + 1) {  // the factor eps / (h + 1 - h)
+        N = e;
+        N1 = {1.0f, 0.0f};
+    } else {  // eps (eps - 1) / ((a - h)(a - h - 1))
+        const ff c = ff_mul(recip_signed(a - h), recip_signed(a - h - 1));
+        N = ff_mul(ff_mul(e, ff_add_f(e, -1.0f)), c);
+        N1 = ff_mul(ff_add_f(ff_add(e, e), -1.0f), c);
+        N2 = 2.0f * c.hi;
+    }
+    const ff W0 = ff_mul(Q, N);
+    const ff W1 = ff_mul(Q, ff_add(ff_mul(S1, N), N1));
+    const float q = Q.hi, s1 = S1.hi, n = N.hi, n1 = N1.hi;
+    const float A2 = s1 * s1 - S2;
+    out[0] = W0.hi;
+    out[1] = W0.lo;
+    out[2] = W1.hi + W1.lo;
+    out[3] = 0.5f * q * (A2 * n + 2.0f * s1 * n1 + N2);
+    out[4] = q * ((s1 * A2 - 2.0f * s1 * S2 + 2.0f * S3) * n + 3.0f * A2 * n1 + 3.0f * s1 * N2) * (1.0f / 6.0f);
+}
+
+// exact float-float weight of tap a at eps (the fallback)
+template <int T>
+__device__ __forceinline__ ff weight_ff(ff e, int a)
+{
+    constexpr int h = (T - 2) / 2;
+    ff w = {1.0f, 0.0f};
+#pragma unroll 1
+    for (int i = 0; i < T; ++i)
+        if (i != a) w = ff_mul(w, ff_mul(ff_add_f(e, (float)(h - i)), recip_signed(a - i)));
+    return w;
+}
+
+constexpr float TAYLOR_MAX_DELTA = 5e-5f;
+
 // Shared memory: Lf[6][WN] (int64, link delays in fixed point samples), Dq[WN] (int64, running
-// chained delay of the current chain), Ghi, Glo [3][WN] (float), Whi, Wlo [T][WN] (float-float
-// weights: with constant delays every output of a term reads with the same fraction, and FP32
-// weight roundings would then act as one fixed filter error that a smooth cotangent sees without
-// the TDI cancellation), Mo[WN] (int).
+// chained delay of the current chain), Ghi, Glo [3][WN] (float), Mo[WN] (int), Dl[WN] (float, the
+// offset of each output's fraction from the term's reference), Rf[42][5][T] (float: W0 hi, W0 lo,
+// W1, W2, W3 of every term and tap).
 template <int T>
 __global__ void __launch_bounds__(256, 2) k_tdi_adj_mx(FwdParams P, BwdParams B)
 {
@@ -129,13 +207,16 @@ __global__ void __launch_bounds__(256, 2) k_tdi_adj_mx(FwdParams P, BwdParams B)
     extern __shared__ __align__(16) long long smi[];
     const int WN = B.wn;
     long long *Lf = smi, *Dq = smi + 6 * WN;
-    float *Ghi = reinterpret_cast<float *>(smi + 7 * WN), *Glo = Ghi + 3 * WN, *Whi = Glo + 3 * WN;
-    float *Wlo = Whi + T * WN;
-    int *Mo = reinterpret_cast<int *>(Wlo + T * WN);
+    float *Ghi = reinterpret_cast<float *>(smi + 7 * WN), *Glo = Ghi + 3 * WN;
+    int *Mo = reinterpret_cast<int *>(Glo + 3 * WN);
+    float *Dl = reinterpret_cast<float *>(Mo + WN);
+    float *Rf = Dl + WN;
     __shared__ TileInfo ti;
     __shared__ int mo_lo, mo_hi;
+    __shared__ unsigned dmax_bits;
     __shared__ unsigned long long gmax;
     __shared__ long long dnest[NTERM_BW];
+    __shared__ long long xref[NTERM_BW];  // each term's read offset at the window centre (fixed point)
     const int64_t total = P.total_tiles >= 0 ? P.total_tiles : P.src.tile_off[P.src.S];
     for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
         if (threadIdx.x == 0) {
@@ -150,6 +231,7 @@ __global__ void __launch_bounds__(256, 2) k_tdi_adj_mx(FwdParams P, BwdParams B)
         }
         const int64_t N = ti.N, k0 = ti.n0, n_lo = k0 - h - 2;
         const int nb = (int)ti.nb, wn = nb + 2 * h + 5 + B.dmax;
+        const int jref = wn / 2;
         const double *gx = B.g_xyz + (ti.out - P.out);
         // link delays of every window output in fixed point; the largest |g| of the window
         unsigned long long mb = 0ull;
@@ -170,9 +252,18 @@ __global__ void __launch_bounds__(256, 2) k_tdi_adj_mx(FwdParams P, BwdParams B)
             const double a = __ldg(P.nest_tab + kk * NTERM_BW + threadIdx.x);
             const double b = __ldg(P.nest_tab + (kk + 1) * NTERM_BW + threadIdx.x);
             dnest[threadIdx.x] = llrint(fma(f, b - a, a) * FX_ONE);
+        } else if (threadIdx.x < NTERM_BW) {
+            dnest[threadIdx.x] = 0;
         }
         block_max_u64(&gmax, mb);
         __syncthreads();
+        // each term's read offset at the window centre
+        if (threadIdx.x < NTERM_BW) {
+            const int id = threadIdx.x, ch = id / 14, c = (id / 7) % 2, q = id % 7 + 1;
+            long long D = 0;
+            for (int qq = 1; qq <= q; ++qq) D += Lf[c_tdibm.pair[ch][c][qq] * WN + jref];
+            xref[id] = -(D + dnest[id]);
+        }
         const int se = scale_exp(gmax);
         const double up = exp2((double)se), down = exp2((double)-se);
         for (int j = threadIdx.x; j < wn; j += blockDim.x) {
@@ -183,6 +274,17 @@ __global__ void __launch_bounds__(256, 2) k_tdi_adj_mx(FwdParams P, BwdParams B)
                 Ghi[c * WN + j] = v.hi;
                 Glo[c * WN + j] = v.lo;
             }
+        }
+        __syncthreads();
+        // reference weights and Taylor coefficients of every (term, tap)
+        for (int t = threadIdx.x; t < NTERM_BW * T; t += blockDim.x) {
+            const int id = t / T, a = t - id * T;
+            if (id % 7 + 1 > P.q_terms) continue;
+            const Split s = split_fx(xref[id]);
+            float out[5];
+            ref_weight_taylor<T>(ff{s.ehi, s.elo}, a, out);
+#pragma unroll
+            for (int f = 0; f < 5; ++f) Rf[(id * 5 + f) * T + a] = out[f];
         }
         ff acc[6];
 #pragma unroll
@@ -205,25 +307,32 @@ __global__ void __launch_bounds__(256, 2) k_tdi_adj_mx(FwdParams P, BwdParams B)
             for (int c = 0; c < 2; ++c) {
                 for (int j = threadIdx.x; j < wn; j += blockDim.x) Dq[j] = 0;
                 for (int q = 1; q <= P.q_terms; ++q) {
+                    const int id = (ch * 2 + c) * 7 + q - 1;
                     if (threadIdx.x == 0) {
                         mo_lo = INT_MAX;
                         mo_hi = INT_MIN;
+                        dmax_bits = 0u;
                     }
                     __syncthreads();
                     const int pl = c_tdibm.pair[ch][c][q];
-                    const long long dn = P.nest_tab ? dnest[(ch * 2 + c) * 7 + q - 1] : 0ll;
+                    const long long xr = xref[id];
                     int lmin = INT_MAX, lmax = INT_MIN;
+                    float dm = 0.0f;
                     for (int j = threadIdx.x; j < wn; j += blockDim.x) {
                         const long long D = Dq[j] + Lf[pl * WN + j];
                         Dq[j] = D;
-                        const Split s = split_fx(-(D + dn));  // read at n - D: index n + m
-                        Mo[j] = s.m;
-                        lmin = min(lmin, s.m);
-                        lmax = max(lmax, s.m);
-                        lagrange_w_ff<T>(ff{s.ehi, s.elo}, Whi + j, Wlo + j, WN);
+                        const long long X = -(D + dnest[id]);  // read at n - D: index n + m
+                        const int m = (int)(X >> FX_BITS);
+                        Mo[j] = m;
+                        lmin = min(lmin, m);
+                        lmax = max(lmax, m);
+                        const float d = (float)(X - xr) * 0x1p-44f;  // exact difference, then rounded
+                        Dl[j] = d;
+                        dm = fmaxf(dm, fabsf(d));
                     }
                     atomicMin(&mo_lo, lmin);
                     atomicMax(&mo_hi, lmax);
+                    atomicMax(&dmax_bits, __float_as_uint(dm));
                     __syncthreads();
                     if (me < nb) {
                         // outputs n whose stencil [n + Mo - h, n + Mo + h + 1] contains k
@@ -231,10 +340,27 @@ __global__ void __launch_bounds__(256, 2) k_tdi_adj_mx(FwdParams P, BwdParams B)
                         jlo = max(jlo, 0);
                         jhi = min(jhi, wn - 1);
                         ff s = {0.0f, 0.0f};
-                        for (int j = jlo; j <= jhi; ++j) {
-                            const int a = (int)(k - (n_lo + j + Mo[j])) + h;
-                            if (a >= 0 && a < T)
-                                ff_fma_acc2(s, Whi[a * WN + j], Wlo[a * WN + j], Ghi[ch * WN + j], Glo[ch * WN + j]);
+                        const bool taylor = mo_lo == mo_hi && mo_lo == (int)(xr >> FX_BITS) &&
+                                            __uint_as_float(dmax_bits) <= TAYLOR_MAX_DELTA;
+                        if (taylor) {
+                            const float *R0h = Rf + (id * 5) * T, *R0l = R0h + T, *R1 = R0l + T, *R2 = R1 + T,
+                                        *R3 = R2 + T;
+                            for (int j = jlo; j <= jhi; ++j) {
+                                const int a = (int)(k - (n_lo + j + mo_lo)) + h;  // in [0, T): one stencil
+                                const float d = Dl[j];
+                                const float corr = d * fmaf(d, fmaf(d, R3[a], R2[a]), R1[a]);
+                                ff_fma_acc2(s, R0h[a], R0l[a] + corr, Ghi[ch * WN + j], Glo[ch * WN + j]);
+                            }
+                        } else {
+                            for (int j = jlo; j <= jhi; ++j) {
+                                const int a = (int)(k - (n_lo + j + Mo[j])) + h;
+                                if (a >= 0 && a < T) {
+                                    const long long X = -(Dq[j] + dnest[id]);
+                                    const Split sp = split_fx(X);
+                                    const ff w = weight_ff<T>(ff{sp.ehi, sp.elo}, a);
+                                    ff_fma_acc2(s, w.hi, w.lo, Ghi[ch * WN + j], Glo[ch * WN + j]);
+                                }
+                            }
                         }
                         const int lk = c_tdibm.link[ch][c][q];
 #pragma unroll
@@ -459,7 +585,8 @@ void *bwd_kernel_mx(int kind, int order)
 size_t smem_bwd_mx(int kind, int order, const BwdParams &B)
 {
     const size_t T = (size_t)order + 1;
-    return kind == 0 ? (size_t)B.wn * (7 * 8 + 6 * 4 + 2 * T * 4 + 4) : (size_t)B.wk * (27 * 8 + 2 * T * 4 + 4);
+    return kind == 0 ? (size_t)B.wn * (7 * 8 + 6 * 4 + 4 + 4) + (size_t)NTERM_BW * 5 * T * 4
+                     : (size_t)B.wk * (27 * 8 + 2 * T * 4 + 4);
 }
 
 int launch_bwd_mx(int kind, int order, const FwdParams &P, const BwdParams &B, int sms, void *stream)
