@@ -24,9 +24,10 @@ constexpr int BWD_TILE_H = 128;  // strain samples per projection-transpose tile
 // kind 0: TDI transpose, 1: projection transpose, 2: sky-gradient partials
 int launch_bwd(int kind, int order, const FwdParams &P, const BwdParams &B, int sms, void *stream);
 size_t smem_bwd(int kind, int order, const FwdParams &P, const BwdParams &B);
-// mixed-precision transposes (kind 0: TDI, 1: projection) for plans of precision LR_MIXED
+// mixed-precision adjoint kernels for plans of precision LR_MIXED (kind 0: TDI transpose, 1:
+// projection transpose, 2: sky-gradient partials)
 int launch_bwd_mx(int kind, int order, const FwdParams &P, const BwdParams &B, int sms, void *stream);
-size_t smem_bwd_mx(int kind, int order, const BwdParams &B);
+size_t smem_bwd_mx(int kind, int order, const FwdParams &P, const BwdParams &B);
 int launch_sky_reduce(const double *partial, const int64_t *tile_off, int64_t S, int64_t ntiles1, double *g_sky,
                       void *stream);
 

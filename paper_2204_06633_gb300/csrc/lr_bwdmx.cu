@@ -567,13 +567,240 @@ __global__ void __launch_bounds__(256, 2) k_proj_adj_mx(FwdParams P, BwdParams B
     }
 }
 
+// ---------------------------------------------------------------- KM3: sky-angle gradient
+// dLoss/d(lambda, beta, psi) = sum over link samples and links of g_y times the derivative of the
+// link response (patterns, 1/(2(1 - k.n)) and the read times through k), as the FP64 kernel, with
+// the strain reads and their derivative reads in float-float: value and derivative weights from
+// float-float prefix and suffix products (product rule), float-float strain (scaled per tile by a
+// power of two).  The geometry and the assembly against g_y stay FP64.
+
+struct LinkGeoN {
+    double xp, xc, kn, den;
+};
+
+__device__ __forceinline__ LinkGeoN link_geo_n(const SkyConst &S, const double *x, int l, double *nvec)
+{
+    const int LR[6] = {0, 1, 2, 0, 2, 1}, LS[6] = {1, 2, 0, 2, 1, 0};
+    const int r = LR[l], s = LS[l];
+    double d0 = x[3 * r] - x[3 * s], d1 = x[3 * r + 1] - x[3 * s + 1], d2 = x[3 * r + 2] - x[3 * s + 2];
+    const double inv = 1.0 / sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    d0 *= inv;
+    d1 *= inv;
+    d2 *= inv;
+    nvec[0] = d0;
+    nvec[1] = d1;
+    nvec[2] = d2;
+    const double un = S.u[0] * d0 + S.u[1] * d1 + S.u[2] * d2;
+    const double vn = S.v[0] * d0 + S.v[1] * d1 + S.v[2] * d2;
+    LinkGeoN g;
+    g.kn = S.k[0] * d0 + S.k[1] * d1 + S.k[2] * d2;
+    const double xip = un * un - vn * vn, xic = 2.0 * un * vn;
+    g.xp = S.c2p * xip + S.s2p * xic;
+    g.xc = -S.s2p * xip + S.c2p * xic;
+    g.den = 1.0 / (2.0 * (1.0 - g.kn));
+    return g;
+}
+
+// value and derivative (d/dposition) of the staged float-float series at window offset st + eps:
+// weights w_a = sgn L_a R_a and dw_a = sgn (L'_a R_a + L_a R'_a) from the prefix / suffix products
+// and their derivatives (every factor (eps + h - i)/d linear in eps, d/deps = 1/d).  The sums are
+// taken on the differences from the centre sample, s_h + sum w_a (s_a - s_h) and sum dw_a (s_a -
+// s_h) (exact rewrites: the weights sum to 1, the derivative weights to 0), so the rounding scales
+// with the small differences of a smooth series and not with the series itself.
+template <int T>
+__device__ void read_vd_ff(const float *phi, const float *plo, const float *chi, const float *clo, int st, ff e,
+                           ff &vp, ff &dp, ff &vc, ff &dc)
+{
+    constexpr int h = (T - 2) / 2;
+    ff Lp[T], Ld[T];
+    ff L = {1.0f, 0.0f}, D = {0.0f, 0.0f};
+#pragma unroll 1
+    for (int a = 0; a < T; ++a) {
+        Lp[a] = L;
+        Ld[a] = D;
+        const ff r = {c_recip.hi[a + 1], c_recip.lo[a + 1]};
+        const ff f = ff_mul(ff_add_f(e, (float)(h - a)), r);
+        D = ff_add(ff_mul(D, f), ff_mul(L, r));
+        L = ff_mul(L, f);
+    }
+    vp = dp = vc = dc = ff{0.0f, 0.0f};
+    const ff cp = {phi[st + h], plo[st + h]}, cc = {chi[st + h], clo[st + h]};
+    ff R = {1.0f, 0.0f}, RD = {0.0f, 0.0f};
+#pragma unroll 1
+    for (int a = T - 1; a >= 0; --a) {
+        ff w = ff_mul(Lp[a], R), dw = ff_add(ff_mul(Ld[a], R), ff_mul(Lp[a], RD));
+        if ((T - 1 - a) & 1) {
+            w = ff_neg(w);
+            dw = ff_neg(dw);
+        }
+        const ff sp = ff_sub(ff{phi[st + a], plo[st + a]}, cp), sc = ff_sub(ff{chi[st + a], clo[st + a]}, cc);
+        ff_fma_acc2(vp, w.hi, w.lo, sp.hi, sp.lo);
+        ff_fma_acc2(dp, dw.hi, dw.lo, sp.hi, sp.lo);
+        ff_fma_acc2(vc, w.hi, w.lo, sc.hi, sc.lo);
+        ff_fma_acc2(dc, dw.hi, dw.lo, sc.hi, sc.lo);
+        const ff r = {c_recip.hi[T - a], c_recip.lo[T - a]};
+        const ff g = ff_mul(ff_add_f(e, (float)(h - a)), r);
+        RD = ff_add(ff_mul(RD, g), ff_mul(R, r));
+        R = ff_mul(R, g);
+    }
+    vp = ff_add(vp, cp);
+    vc = ff_add(vc, cc);
+}
+
+// reads at window offset base + u (FP64 position): index split in FP64, fraction as float-float;
+// results unscaled to FP64.  An out-of-window stencil records ERR_WINDOW and reads 0.
+template <int T>
+__device__ __forceinline__ void read_vd_mx(const float *sm, int wstride, int64_t base, double u, int64_t w_lo,
+                                           int wlen, double down, int *err, double &vp, double &dp, double &vc,
+                                           double &dc)
+{
+    constexpr int h = (T - 2) / 2;
+    const double fl = floor(u);
+    const int64_t st = base + (int64_t)fl - h - w_lo;
+    vp = dp = vc = dc = 0.0;
+    if (st < 0 || st + T > wlen) {
+        atomicOr(err, ERR_WINDOW);
+        return;
+    }
+    const double ed = u - fl;
+    const float eh = __double2float_rn(ed);
+    ff a, b, c, d;
+    read_vd_ff<T>(sm, sm + wstride, sm + 2 * wstride, sm + 3 * wstride, (int)st, ff{eh, __double2float_rn(ed - eh)}, a,
+                  b, c, d);
+    vp = ((double)a.hi + (double)a.lo) * down;
+    dp = ((double)b.hi + (double)b.lo) * down;
+    vc = ((double)c.hi + (double)c.lo) * down;
+    dc = ((double)d.hi + (double)d.lo) * down;
+}
+
+template <int T>
+__global__ void __launch_bounds__(256) k_sky_adj_mx(FwdParams P, BwdParams B)
+{
+    constexpr int h = (T - 2) / 2;
+    extern __shared__ __align__(16) float sms[];  // h+ hi, h+ lo, hx hi, hx lo: [4][wmax]
+    const int WS = P.wmax;
+    __shared__ TileInfo ti;
+    __shared__ SkyConst skc;
+    __shared__ double red[3][8];
+    __shared__ double dk[2][3], du[2][3], dv[2][3];
+    __shared__ unsigned long long hmax;
+    const int64_t total = P.total_tiles >= 0 ? P.total_tiles : P.src.tile_off[P.src.S];
+    for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+        if (threadIdx.x == 0) {
+            ti = tile_info(P, g, 3);
+            if (!ti.ok) atomicOr(P.err, ERR_OFFSETS);
+            skc = make_sky(ti.sky);
+            hmax = 0ull;
+            double sl, cl, sb, cb;
+            sincos(ti.sky.lam, &sl, &cl);
+            sincos(ti.sky.beta, &sb, &cb);
+            // derivatives of k = -e_r, u = -e_phi, v = -e_theta with respect to lambda, beta
+            dk[0][0] = cb * sl;  dk[0][1] = -cb * cl; dk[0][2] = 0.0;
+            dk[1][0] = sb * cl;  dk[1][1] = sb * sl;  dk[1][2] = -cb;
+            du[0][0] = cl;       du[0][1] = sl;       du[0][2] = 0.0;
+            du[1][0] = 0.0;      du[1][1] = 0.0;      du[1][2] = 0.0;
+            dv[0][0] = sb * sl;  dv[0][1] = -sb * cl; dv[0][2] = 0.0;
+            dv[1][0] = -cb * cl; dv[1][1] = -cb * sl; dv[1][2] = -sb;
+        }
+        __syncthreads();
+        double G[3] = {0.0, 0.0, 0.0};
+        if (ti.ok && ti.nb > 0) {
+            const int ny = (int)ti.nb;
+            const double u0 = (P.t0 - ti.t0h) / P.dt;
+            const int64_t w_lo = ti.n0 + (int64_t)floor(u0) - P.sig_b - P.lproj_b - h - 2;
+            const int wlen = ny + 2 * P.sig_b + P.lproj_b + T + 4;
+            unsigned long long mb = 0ull;
+            for (int j = threadIdx.x; j < wlen; j += blockDim.x) {
+                const int64_t i = w_lo + j;
+                const bool in = i >= 0 && i < ti.nh;
+                mb = max(mb, in ? max(abs_bits64(__ldg(ti.hp + i)), abs_bits64(__ldg(ti.hc + i))) : 0ull);
+            }
+            block_max_u64(&hmax, mb);
+            __syncthreads();
+            const int se = scale_exp(hmax);
+            const double up = exp2((double)se), down = exp2((double)-se);
+            for (int j = threadIdx.x; j < wlen; j += blockDim.x) {
+                const int64_t i = w_lo + j;
+                const bool in = i >= 0 && i < ti.nh;
+                const ff a = in ? ff_scaled(__ldg(ti.hp + i), up) : ff{0.0f, 0.0f};
+                const ff b = in ? ff_scaled(__ldg(ti.hc + i), up) : ff{0.0f, 0.0f};
+                sms[j] = a.hi;
+                sms[WS + j] = a.lo;
+                sms[2 * WS + j] = b.hi;
+                sms[3 * WS + j] = b.lo;
+            }
+            __syncthreads();
+            const double *gy = B.g_y + 6 * (ti.out - P.out) / 3;
+            for (int jj = threadIdx.x; jj < ny; jj += blockDim.x) {
+                const int64_t k = ti.n0 + jj;
+                double x[9], L[6];
+                orbit_all(P.po, P.t0 + (double)k * P.dt, x, L);
+                double sig[3];
+                for (int i = 0; i < 3; ++i)
+                    sig[i] = (skc.k[0] * x[3 * i] + skc.k[1] * x[3 * i + 1] + skc.k[2] * x[3 * i + 2]) / C_LIGHT *
+                             P.inv_dt;
+                double Rp[3], Rpd[3], Rc[3], Rcd[3];
+                for (int r = 0; r < 3; ++r)
+                    read_vd_mx<T>(sms, WS, k, u0 - sig[r], w_lo, wlen, down, P.err, Rp[r], Rpd[r], Rc[r], Rcd[r]);
+                for (int l = 0; l < 6; ++l) {
+                    const double gl = __ldg(gy + l * ti.N + k);
+                    if (gl == 0.0) continue;
+                    const int LR[6] = {0, 1, 2, 0, 2, 1}, LS[6] = {1, 2, 0, 2, 1, 0};
+                    const int r = LR[l], s = LS[l];
+                    double nv[3];
+                    const LinkGeoN q = link_geo_n(skc, x, l, nv);
+                    double ep, epd, ec, ecd;
+                    read_vd_mx<T>(sms, WS, k, u0 - L[l] * P.inv_dt - sig[s], w_lo, wlen, down, P.err, ep, epd, ec, ecd);
+                    const double dPp = ep - Rp[r], dPc = ec - Rc[r];
+                    const double dH = q.xp * dPp + q.xc * dPc;
+                    const double un = skc.u[0] * nv[0] + skc.u[1] * nv[1] + skc.u[2] * nv[2];
+                    const double vn = skc.v[0] * nv[0] + skc.v[1] * nv[1] + skc.v[2] * nv[2];
+                    for (int th = 0; th < 2; ++th) {
+                        const double da = du[th][0] * nv[0] + du[th][1] * nv[1] + du[th][2] * nv[2];
+                        const double db = dv[th][0] * nv[0] + dv[th][1] * nv[1] + dv[th][2] * nv[2];
+                        const double dxip = 2.0 * (un * da - vn * db), dxic = 2.0 * (da * vn + un * db);
+                        const double dxp = skc.c2p * dxip + skc.s2p * dxic, dxc = -skc.s2p * dxip + skc.c2p * dxic;
+                        const double dkn = dk[th][0] * nv[0] + dk[th][1] * nv[1] + dk[th][2] * nv[2];
+                        const double dden = 2.0 * q.den * q.den * dkn;
+                        const double due = -(dk[th][0] * x[3 * s] + dk[th][1] * x[3 * s + 1] + dk[th][2] * x[3 * s + 2]) /
+                                           C_LIGHT * P.inv_dt;
+                        const double dur = -(dk[th][0] * x[3 * r] + dk[th][1] * x[3 * r + 1] + dk[th][2] * x[3 * r + 2]) /
+                                           C_LIGHT * P.inv_dt;
+                        const double ddH = dxp * dPp + dxc * dPc + q.xp * (epd * due - Rpd[r] * dur) +
+                                           q.xc * (ecd * due - Rcd[r] * dur);
+                        G[th] = fma(gl, dden * dH + q.den * ddH, G[th]);
+                    }
+                    G[2] = fma(gl, q.den * (2.0 * q.xc * dPp - 2.0 * q.xp * dPc), G[2]);
+                }
+            }
+        }
+        // fixed-order block reduction: warp tree, then warps in order
+        for (int t = 0; t < 3; ++t) {
+            double v = G[t];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if ((threadIdx.x & 31) == 0) red[t][threadIdx.x >> 5] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int t = 0; t < 3; ++t) {
+                double acc = 0.0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += red[t][w];
+                B.partial[3 * g + t] = acc;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 #define LR_BM_ORDERS(X) X(1) X(3) X(5) X(7) X(9) X(11) X(13) X(15) X(17) X(19) X(21) X(23) X(25) X(31) X(41)
 
 void *bwd_kernel_mx(int kind, int order)
 {
     switch (order) {
 #define LR_CASE(p) \
-    case p: return kind == 0 ? (void *)k_tdi_adj_mx<p + 1> : (void *)k_proj_adj_mx<p + 1>;
+    case p: return kind == 0 ? (void *)k_tdi_adj_mx<p + 1> : kind == 1 ? (void *)k_proj_adj_mx<p + 1> \
+                                                                        : (void *)k_sky_adj_mx<p + 1>;
         LR_BM_ORDERS(LR_CASE)
 #undef LR_CASE
         default: return nullptr;
@@ -582,9 +809,10 @@ void *bwd_kernel_mx(int kind, int order)
 
 }  // namespace
 
-size_t smem_bwd_mx(int kind, int order, const BwdParams &B)
+size_t smem_bwd_mx(int kind, int order, const FwdParams &P, const BwdParams &B)
 {
     const size_t T = (size_t)order + 1;
+    if (kind == 2) return sizeof(float) * 4 * (size_t)P.wmax;
     return kind == 0 ? (size_t)B.wn * (7 * 8 + 6 * 4 + 4 + 4) + (size_t)NTERM_BW * 5 * T * 4
                      : (size_t)B.wk * (27 * 8 + 2 * T * 4 + 4);
 }
@@ -593,7 +821,7 @@ int launch_bwd_mx(int kind, int order, const FwdParams &P, const BwdParams &B, i
 {
     void *k = bwd_kernel_mx(kind, order);
     if (!k) return (int)cudaErrorInvalidValue;
-    const size_t smem = smem_bwd_mx(kind, order, B);
+    const size_t smem = smem_bwd_mx(kind, order, P, B);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     int per_sm = 0;

@@ -723,10 +723,10 @@ int backward_launch(lr_plan *plan, lr::FwdParams &P, lr::BwdParams &B, int64_t S
 {
     const int sms = plan->ctx->sms;
     const int order = plan->desc.order;
-    // mixed plans: the TDI and projection transposes in mixed precision, the sky gradient in FP64
+    // mixed plans: the transposes and the sky gradient in the mixed kernels
     const bool mx = plan->desc.precision == LR_MIXED;
     int e = mx ? lr::launch_bwd_mx(0, order, P, B, sms, stream) : lr::launch_bwd(0, order, P, B, sms, stream);
-    if (!e && g_sky) e = lr::launch_bwd(2, order, P, B, sms, stream);
+    if (!e && g_sky) e = mx ? lr::launch_bwd_mx(2, order, P, B, sms, stream) : lr::launch_bwd(2, order, P, B, sms, stream);
     if (!e) e = mx ? lr::launch_bwd_mx(1, order, P, B, sms, stream) : lr::launch_bwd(1, order, P, B, sms, stream);
     if (!e && g_sky) e = lr::launch_sky_reduce(B.partial, ktile_off, S, P.total_tiles, g_sky, stream);
     return check_launch(plan->ctx, e);
