@@ -16,12 +16,16 @@
 // Each tile's cotangents are scaled by a power of two (exactly) so that FP32 neither overflows nor
 // underflows; the results are unscaled exactly.
 //
+//   KM3  dLoss/d(lambda, beta, psi)   tile of 256 link samples; the FP64 geometry per sample,
+//                          the strain reads and their derivative reads in float-float, the assembly
+//                          against g_y in FP64; per-tile partials summed in order by the FP64
+//                          reduction kernel.
+//
 // Accuracy: the weights are float-float (~2^-45 relative), not FP32: with a static constellation
 // or constant delays every read of a term has the same fraction, and FP32 weight roundings would
 // act as one fixed filter error that a smooth part of the cotangent (the signal mismatch of a
 // residual) sees without the cancellation of the transposed operators; the sky-angle gradient, a
-// sum that cancels strongly, then moved by ~1e-6.  The sky-angle gradient of a mixed plan runs in
-// the FP64 kernel on this g_y.
+// sum that cancels strongly, then moved by ~1e-6.
 #include <cuda_runtime.h>
 
 #include <climits>

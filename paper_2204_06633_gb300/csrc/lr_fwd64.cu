@@ -155,13 +155,20 @@ __device__ inline void stage_checked(double *dst, const double *src, int64_t lo,
     if (bad) atomicOr(err, ERR_NONFINITE);
 }
 
+// generated strain window (out of line: keeps the sincos out of the hot body)
+__device__ __noinline__ void stage_generated64(const GbConst &g, double t0, double dt, int64_t lo, int len, double *hwp,
+                                               double *hwc)
+{
+    for (int j = threadIdx.x; j < len; j += blockDim.x) gb_strain(g, t0, dt, lo + j, hwp[j], hwc[j]);
+}
+
 // the strain window of a tile: staged from the caller's arrays, or generated (Galactic binary on
 // the output grid, strain index = output index)
 __device__ inline void stage_strain(const FwdParams &P, const TileInfo &ti, double *hwp, double *hwc, int64_t lo,
                                     int len)
 {
     if (P.gen_strain) {
-        for (int j = threadIdx.x; j < len; j += blockDim.x) gb_strain(ti.gb, P.t0, P.dt, lo + j, hwp[j], hwc[j]);
+        stage_generated64(ti.gb, P.t0, P.dt, lo, len, hwp, hwc);
     } else {
         stage_checked(hwp, ti.hp, lo, len, ti.nh, P.err);
         stage_checked(hwc, ti.hc, lo, len, ti.nh, P.err);

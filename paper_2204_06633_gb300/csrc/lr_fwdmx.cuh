@@ -500,6 +500,23 @@ __device__ void build_tables(float *smf, int base0, int AS, int SS, int nser, in
     }
 }
 
+// Generated strain window of a tile (Galactic binary on the output grid): out of line, so the
+// double-double phase and the sincos stay out of the hot body of kernels that read strain arrays.
+// Returns this thread's largest bit pattern of |h|.
+__device__ __noinline__ unsigned long long stage_generated(const GbConst &g, double t0, double dt, int64_t i0,
+                                                           int wlen, double *pf)
+{
+    unsigned long long mx = 0ull;
+    for (int j = threadIdx.x; j < wlen; j += blockDim.x) {
+        double a, b;
+        gb_strain(g, t0, dt, i0 + j, a, b);
+        pf[j] = a;
+        pf[MX_WCAP + j] = b;
+        mx = max(mx, max(abs_bits(a), abs_bits(b)));
+    }
+    return mx;
+}
+
 // ---------------------------------------------------------------- per-tile setup
 // Tile g's bookkeeping (one thread): source, offsets, sky frame, span.
 template <int KIND>
@@ -1212,19 +1229,17 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
             const int woff = wok ? ts.wlo - h - 2 : 0;
             woff_fx = (long long)woff << FX_BITS;
             unsigned long long mx = 0ull;
-            for (int j = tid; j < wlen; j += blockDim.x) {
-                const int64_t i = ts.k_lo + woff + j;
-                double a, b;
-                if (P.gen_strain) {  // the Galactic binary generated at t0 + i dt
-                    gb_strain(ts.ti.gb, P.t0, P.dt, i, a, b);
-                } else {
+            if (P.gen_strain) {  // the Galactic binary generated at t0 + i dt
+                mx = stage_generated(ts.ti.gb, P.t0, P.dt, ts.k_lo + woff, wlen, pf);
+            } else {
+                for (int j = tid; j < wlen; j += blockDim.x) {
+                    const int64_t i = ts.k_lo + woff + j;
                     const bool in = i >= 0 && i < ts.ti.nh;
-                    a = in ? __ldg(ts.ti.hp + i) : 0.0;
-                    b = in ? __ldg(ts.ti.hc + i) : 0.0;
+                    const double a = in ? __ldg(ts.ti.hp + i) : 0.0, b = in ? __ldg(ts.ti.hc + i) : 0.0;
+                    pf[j] = a;
+                    pf[MX_WCAP + j] = b;
+                    mx = max(mx, max(abs_bits(a), abs_bits(b)));
                 }
-                pf[j] = a;
-                pf[MX_WCAP + j] = b;
-                mx = max(mx, max(abs_bits(a), abs_bits(b)));
             }
             block_absmax(&ts.maxbits, mx);
             __syncthreads();
