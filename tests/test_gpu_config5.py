@@ -1,8 +1,8 @@
 """Mixed-precision batched forward + backward at full size: 256 one-year sources (N = 3 153 600
 each, parameters drawn as for the batched workload, seed 5), flexing orbit, order 41, in the
 launch configuration of the batched calls.  Forward: every source's X, Y, Z at sampled outputs
-against the oracle (relative L2 <= 1e-6 per source).  Backward (the mixed adjoint: FP32 taps
-and float-float sums in the transposes, the sky gradient in FP64): the batched dot-product identity <R h, g> = <h, R^T g> with the mixed
+against the oracle (relative L2 <= 1e-6 per source).  Backward (the mixed adjoint: float-float
+weights and sums in the transposes and the sky-angle reads, geometry in FP64): the batched dot-product identity <R h, g> = <h, R^T g> with the mixed
 forward, which holds at any size to the forward's own accuracy, and per source the gradients of
 a cotangent on a window of 4000 outputs (zero elsewhere) against the oracle's gradients of the same
 cotangent on a sub-span around the window (the gradients of such a cotangent vanish outside the
