@@ -227,6 +227,10 @@ struct MxShared {
 // nodes on the first 12 of warp 7 (in fused and projection launches these warps have one
 // projection item and are free for the next tile's setup while the others finish theirs)
 constexpr int SETUP_PIECE0 = 192, SETUP_GEO0 = 224;
+// TDI reference lanes of fused launches: a link span holds at most MX_YCAP <= 2 x 256 - 128
+// samples, so threads 128 .. 169 have one sample of the link loop and are free for a second
+static_assert(MX_YCAP <= MIXED_THREADS + 128, "the TDI reference lanes have a single link sample");
+constexpr int TDI_REF0 = 128;
 
 // ---------------------------------------------------------------- helpers
 __device__ inline const double *orbit_coef_ptr(const OrbitDev &o, int K, int s)
@@ -502,12 +506,12 @@ __device__ void build_tables(float *smf, int base0, int AS, int SS, int nser, in
 
 // Generated strain window of a tile (Galactic binary on the output grid): out of line, so the
 // double-double phase and the sincos stay out of the hot body of kernels that read strain arrays.
-// Returns this thread's largest bit pattern of |h|.
+// Samples j0, j0 + stride, ...; returns this thread's largest bit pattern of |h|.
 __device__ __noinline__ unsigned long long stage_generated(const GbConst &g, double t0, double dt, int64_t i0,
-                                                           int wlen, double *pf)
+                                                           int wlen, double *pf, int j0, int stride)
 {
     unsigned long long mx = 0ull;
-    for (int j = threadIdx.x; j < wlen; j += blockDim.x) {
+    for (int j = j0; j < wlen; j += stride) {
         double a, b;
         gb_strain(g, t0, dt, i0 + j, a, b);
         pf[j] = a;
@@ -689,12 +693,12 @@ __device__ __forceinline__ void setup_lanes(const FwdParams &P, TileSetup &ts)
 
 // Reference of each delayed TDI term at the tile centre ic (its chained delay is the sum of the
 // pieces' centre values, exactly what the delay table holds at ic) and the correction weights
-// there with their derivative, interleaved as (U_a, dU_a/deps) pairs (the last 42 threads: in
-// fused launches they have no strain-table item).
+// there with their derivative, interleaved as (U_a, dU_a/deps) pairs; threads first ..
+// first + 41, one term each.
 template <int T>
-__device__ void tdi_refs(const FwdParams &P, const TileSetup &ts, MxShared &sh, float *tw)
+__device__ void tdi_refs(const FwdParams &P, const TileSetup &ts, MxShared &sh, float *tw, int first)
 {
-    const int id = threadIdx.x - (MIXED_THREADS - NTERM);
+    const int id = threadIdx.x - first;
     if (id < 0 || id >= NTERM) return;
     const int ch = id / 14, c = (id / 7) % 2, q = id % 7 + 1;
     if (q > P.q_terms) return;
@@ -1228,11 +1232,16 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
             if (!wok && tid == 0) atomicOr(P.err, ERR_WINDOW);
             const int woff = wok ? ts.wlo - h - 2 : 0;
             woff_fx = (long long)woff << FX_BITS;
+            // the CTA's next tile's bookkeeping (a chain of dependent loads) on the last thread,
+            // hidden behind the others' staging loads
+            const int nst = next ? MIXED_THREADS - 1 : MIXED_THREADS;
             unsigned long long mx = 0ull;
-            if (P.gen_strain) {  // the Galactic binary generated at t0 + i dt
-                mx = stage_generated(ts.ti.gb, P.t0, P.dt, ts.k_lo + woff, wlen, pf);
+            if (tid >= nst) {
+                tile_begin<KIND>(P, sh, tn, gn);
+            } else if (P.gen_strain) {  // the Galactic binary generated at t0 + i dt
+                mx = stage_generated(ts.ti.gb, P.t0, P.dt, ts.k_lo + woff, wlen, pf, tid, nst);
             } else {
-                for (int j = tid; j < wlen; j += blockDim.x) {
+                for (int j = tid; j < wlen; j += nst) {
                     const int64_t i = ts.k_lo + woff + j;
                     const bool in = i >= 0 && i < ts.ti.nh;
                     const double a = in ? __ldg(ts.ti.hp + i) : 0.0, b = in ? __ldg(ts.ti.hc + i) : 0.0;
@@ -1254,7 +1263,7 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
                     mx = max(mx, abs_bits(v));
                 }
             block_absmax(&ts.maxbits, mx);
-            tdi_refs<T>(P, ts, sh, smf + OFF_TW);
+            tdi_refs<T>(P, ts, sh, smf + OFF_TW, MIXED_THREADS - NTERM);
             __syncthreads();
         }
         // ---- scaled float-float values
@@ -1290,8 +1299,6 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
         if (KIND != KIND_TDI) {
             // ---- strain difference tables
             build_tables<true, RLW, 4>(smf, warr(0, A_SHI), MX_AW, 7 * MX_AW, 2, wlen);
-            if (FUSED) tdi_refs<T>(P, ts, sh, smf + OFF_TW);
-            if (next && tid == MIXED_THREADS - 1) tile_begin<KIND>(P, sh, tn, gn);
             __syncthreads();
             // ---- projection reads; then, on the warps with one item: the TDI references and
             //      the next tile's setup
@@ -1336,6 +1343,8 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
                     }
                 }
             }
+            // the TDI references of this tile, on threads that the loop above gave one sample
+            if (FUSED) tdi_refs<T>(P, ts, sh, smf + OFF_TW, TDI_REF0);
         }
         double *ld = reinterpret_cast<double *>(smf + OFF_LD);
         if (KIND != KIND_PROJECT) {
