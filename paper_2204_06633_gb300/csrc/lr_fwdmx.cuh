@@ -10,14 +10,16 @@
 //  stage    the strain window (TDI-only launches: the link series) in FP64 and its maximum;
 //           the reference fraction of every delayed TDI term and its correction weights.
 //  convert  scaled by a power of two to float-float, in the 8-phase layout.
-//  tables   first, second and third differences of the staged series.
+//  tables   first, second and third differences of the staged series (two series per thread on
+//           the lanes of packed f32x2 pairs).
 //  project  work item = one read position x 8 consecutive samples: exact fixed-point positions
 //           and index splits, one set of correction weights and its exact derivative per item
 //           (the fraction drifts by the Doppler rate ~1e-4 per sample), an FIR over a register
 //           window of third differences, a float-float anchor; both polarisations.
 //  links    y_l = c+_l (h+(emission) - h+(reception)) + cx_l (hx(emission) - hx(reception)) in
-//           float-float, in place; the per-sample link delays of the tile in fixed point.
-//  tables   of the six link series.
+//           float-float, in place, two links with a common receiver per packed pair; the
+//           per-sample link delays of the tile in fixed point.
+//  tables   of the six link series (three pairs).
 //  TDI      work item = one channel x 4 consecutive outputs: both Michelson chains summed into
 //           one compensated accumulator; each delayed read uses the tile reference weights and
 //           their derivative (a first-order expansion in the fraction, which drifts by ~1e-7 per
@@ -124,6 +126,44 @@ __device__ __forceinline__ void two_sum2(unsigned long long a, unsigned long lon
 enum { A_SHI = 0, A_SLO, A_DHI, A_DLO, A_A, A_E, A_ALO };
 
 // 8-byte asynchronous global -> shared copy (completion: cp_async_wait_all by the issuing thread)
+// float-float arithmetic on both lanes of packed pairs: each lane performs exactly the IEEE
+// operations of the scalar ff_add / ff_sub / ff_mul (lr_mixed.cuh), so results are identical
+struct ff2 {
+    unsigned long long hi, lo;
+};
+
+__device__ __forceinline__ ff2 fast_two_sum2(unsigned long long a, unsigned long long b)
+{
+    const unsigned long long s = fadd2(a, b);
+    return {s, fsub2(b, fsub2(s, a))};
+}
+
+__device__ __forceinline__ ff2 ff_add2(ff2 a, ff2 b)
+{
+    unsigned long long s, e;
+    two_sum2(a.hi, b.hi, s, e);
+    return fast_two_sum2(s, fadd2(e, fadd2(a.lo, b.lo)));
+}
+
+// a - b as a + (-b): the negation is exact, so each operation below rounds as its scalar
+// counterpart with the negated operand
+__device__ __forceinline__ ff2 ff_sub2(ff2 a, ff2 b)
+{
+    const unsigned long long s = fsub2(a.hi, b.hi);
+    const unsigned long long bb = fsub2(s, a.hi);
+    const unsigned long long e = fsub2(fsub2(a.hi, fsub2(s, bb)), fadd2(b.hi, bb));
+    return fast_two_sum2(s, fadd2(e, fsub2(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ ff2 ff_mul2(ff2 a, ff2 b)
+{
+    const unsigned long long p = fmul2(a.hi, b.hi);
+    unsigned long long e = ffma2(a.hi, b.hi, fneg2(p));
+    e = ffma2(a.hi, b.lo, e);
+    e = ffma2(a.lo, b.hi, e);
+    return fast_two_sum2(p, e);
+}
+
 __device__ __forceinline__ void cp_async8(void *dst, const void *src)
 {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -358,21 +398,6 @@ __device__ inline void mx_tile(const FwdParams &P, int64_t g, int ochan, int64_t
 }
 
 
-// value of a fitted geometry factor at tau: constant and linear term in float-float (near a sky
-// direction along an arm 1/(1 - k.n) changes by a large fraction over one tile), the quadratic
-// and cubic terms in FP32
-__device__ __forceinline__ ff geom_at(const TileSetup &ts, int f, float tau)
-{
-    // g0 + g1 tau: exact product of the high parts, one two_sum; every lower-order piece (the
-    // low parts, the product's rounding error, the FP32 quadratic and cubic terms) gathered in
-    // the low word (an unnormalised pair, which the float-float product that follows accepts)
-    const float p = ts.g1h[f] * tau;
-    const float pe = fmaf(ts.g1h[f], tau, -p);
-    const ff s = two_sum(ts.g0h[f], p);
-    const float q = tau * tau * fmaf(tau, ts.g3[f], ts.g2[f]);
-    return {s.hi, s.lo + (fmaf(ts.g1l[f], tau, ts.g0l[f]) + (pe + q))};
-}
-
 // block max of the bit patterns b of |v| (for non-negative doubles the order of the patterns is
 // the order of the values; a NaN orders above every finite value)
 __device__ __forceinline__ unsigned long long abs_bits(double v)
@@ -448,57 +473,75 @@ __device__ __forceinline__ double f2d_pow2(float f, int k)
 __device__ __forceinline__ double ff2d_scaled(float hi, float lo, int se) { return f2d_scaled(hi, se) + f2d_scaled(lo, se); }
 
 
-// Difference tables of a staged float-float series (arrays at base + k * AS, 8-phase index
-// with row length RL): d = s_{j+1} - s_j and a = (d_j - d_{j-1})/2 in float-float (ALO: the low
-// part of a kept in its own array, else folded into a), e = d_{j+2} - 2 d_{j+1} + d_j in FP32.
-// Each thread forms Q consecutive entries of one of the nser series (series stride SS) from one
-// set of differences.  Entries whose stencils leave [0, len) are 0; no read ever uses them.
+// Difference tables of staged float-float series (arrays at base + k * AS, 8-phase index with
+// row length RL): d = s_{j+1} - s_j and a = (d_j - d_{j-1})/2 in float-float (ALO: the low part
+// of a kept in its own array, else folded into a), e = d_{j+2} - 2 d_{j+1} + d_j in FP32.
+// Two series at once, p and p + npair (series stride SS), on the two lanes of packed pairs, each
+// lane the scalar float-float arithmetic; each thread forms Q consecutive entries of a pair from
+// one set of differences.  Entries whose stencils leave [0, len) are 0; no read ever uses them.
 template <bool ALO, int RL, int Q>
-__device__ void build_tables(float *smf, int base0, int AS, int SS, int nser, int len)
+__device__ void build_tables2(float *smf, int base0, int AS, int SS, int npair, int len)
 {
     auto at = [](int i) { return (i & 7) * RL + (i >> 3); };
     const int nq = (len + Q - 1) / Q;
-    for (int it = threadIdx.x; it < nser * nq; it += blockDim.x) {
-        const int ser = it / nq, t = it - ser * nq;
-        const int base = base0 + ser * SS;
+    const unsigned long long HALF = f2pack(0.5f, 0.5f);
+    for (int it = threadIdx.x; it < npair * nq; it += blockDim.x) {
+        const int pr = it / nq, t = it - pr * nq;
+        const int b0 = base0 + pr * SS, b1 = base0 + (pr + npair) * SS;
         const int j0 = Q * t;
-        ff s[Q + 4];  // s_{j0-1} .. s_{j0+Q+2}
+        ff2 s[Q + 4];  // s_{j0-1} .. s_{j0+Q+2}
 #pragma unroll
         for (int u = 0; u < Q + 4; ++u) {
             const int i = j0 - 1 + u;
-            s[u] = (i >= 0 && i < len) ? ff{smf[base + at(i)], smf[base + AS + at(i)]} : ff{0.0f, 0.0f};
+            const bool in = i >= 0 && i < len;
+            const int p = in ? at(i) : 0;
+            s[u] = in ? ff2{f2pack(smf[b0 + p], smf[b1 + p]), f2pack(smf[b0 + AS + p], smf[b1 + AS + p])}
+                      : ff2{0ull, 0ull};
         }
-        ff d[Q + 3], dd[Q + 2];  // d_{j0-1+u}, dd_{j0-1+u} = d_{j0+u} - d_{j0-1+u}
+        ff2 d[Q + 3], dd[Q + 2];
 #pragma unroll
-        for (int u = 0; u < Q + 3; ++u) d[u] = ff_sub(s[u + 1], s[u]);
+        for (int u = 0; u < Q + 3; ++u) d[u] = ff_sub2(s[u + 1], s[u]);
 #pragma unroll
-        for (int u = 0; u < Q + 2; ++u) dd[u] = ff_sub(d[u + 1], d[u]);
+        for (int u = 0; u < Q + 2; ++u) dd[u] = ff_sub2(d[u + 1], d[u]);
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             const int j = j0 + k;
             if (j >= len) break;
-            float dh = 0.0f, dl = 0.0f, a = 0.0f, al = 0.0f, e = 0.0f;
+            unsigned long long DH = 0ull, DL = 0ull, A = 0ull, AL = 0ull, E = 0ull;
             if (j + 1 < len) {
-                dh = d[k + 1].hi;
-                dl = d[k + 1].lo;
+                DH = d[k + 1].hi;
+                DL = d[k + 1].lo;
                 if (j >= 1) {
-                    a = 0.5f * dd[k].hi;
-                    al = 0.5f * dd[k].lo;
+                    A = fmul2(HALF, dd[k].hi);
+                    AL = fmul2(HALF, dd[k].lo);
                 }
                 if (j + 3 < len) {
-                    const ff e3 = ff_sub(dd[k + 2], dd[k + 1]);
-                    e = e3.hi + e3.lo;
+                    const ff2 e3 = ff_sub2(dd[k + 2], dd[k + 1]);
+                    E = fadd2(e3.hi, e3.lo);
                 }
             }
             const int p = at(j);
-            smf[base + A_DHI * AS + p] = dh;
-            smf[base + A_DLO * AS + p] = dl;
-            smf[base + A_E * AS + p] = e;
+            float x0, x1;
+            f2unpack(DH, x0, x1);
+            smf[b0 + A_DHI * AS + p] = x0;
+            smf[b1 + A_DHI * AS + p] = x1;
+            f2unpack(DL, x0, x1);
+            smf[b0 + A_DLO * AS + p] = x0;
+            smf[b1 + A_DLO * AS + p] = x1;
+            f2unpack(E, x0, x1);
+            smf[b0 + A_E * AS + p] = x0;
+            smf[b1 + A_E * AS + p] = x1;
             if (ALO) {
-                smf[base + A_A * AS + p] = a;
-                smf[base + A_ALO * AS + p] = al;
+                f2unpack(A, x0, x1);
+                smf[b0 + A_A * AS + p] = x0;
+                smf[b1 + A_A * AS + p] = x1;
+                f2unpack(AL, x0, x1);
+                smf[b0 + A_ALO * AS + p] = x0;
+                smf[b1 + A_ALO * AS + p] = x1;
             } else {
-                smf[base + A_A * AS + p] = a + al;
+                f2unpack(fadd2(A, AL), x0, x1);
+                smf[b0 + A_A * AS + p] = x0;
+                smf[b1 + A_A * AS + p] = x1;
             }
         }
     }
@@ -1298,7 +1341,7 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
         float *dLf = smf + OFF_W + 2 * 6 * LB;
         if (KIND != KIND_TDI) {
             // ---- strain difference tables
-            build_tables<true, RLW, 4>(smf, warr(0, A_SHI), MX_AW, 7 * MX_AW, 2, wlen);
+            build_tables2<true, RLW, 4>(smf, warr(0, A_SHI), MX_AW, 7 * MX_AW, 1, wlen);
             __syncthreads();
             // ---- projection reads; then, on the warps with one item: the TDI references and
             //      the next tile's setup
@@ -1319,14 +1362,41 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
                 }
                 const float tau = (float)(j - ts.jc) * TAU_UNIT;
                 ff y[6];
+                // links in pairs with a common receiving spacecraft r, (0, 3), (1, 5), (2, 4), on
+                // the two lanes of packed pairs (each lane the scalar float-float arithmetic)
+                const unsigned long long TT = f2pack(tau, tau), TT2 = fmul2(TT, TT);
 #pragma unroll
-                for (int l = 0; l < 6; ++l) {
-                    const int rd = 3 + l;
-                    const ff ep = {smf[OFF_Y + (4 * rd + 0) * MX_AY + ai], smf[OFF_Y + (4 * rd + 1) * MX_AY + ai]};
-                    const ff ec = {smf[OFF_Y + (4 * rd + 2) * MX_AY + ai], smf[OFF_Y + (4 * rd + 3) * MX_AY + ai]};
-                    const int r = l < 3 ? l : (l == 3 ? 0 : (l == 4 ? 2 : 1));  // receiving spacecraft
-                    y[l] = ff_add(ff_mul(geom_at(ts, l, tau), ff_sub(ep, rp[r])),
-                                  ff_mul(geom_at(ts, 6 + l, tau), ff_sub(ec, rc[r])));
+                for (int r = 0; r < 3; ++r) {
+                    const int l0 = r, l1 = r == 0 ? 3 : (r == 1 ? 5 : 4);
+                    auto ld2 = [&](int row) {
+                        return f2pack(smf[OFF_Y + (4 * (3 + l0) + row) * MX_AY + ai],
+                                      smf[OFF_Y + (4 * (3 + l1) + row) * MX_AY + ai]);
+                    };
+                    // geometry factor pair at tau: the constant and linear term in float-float (near
+                    // a sky direction along an arm 1/(1 - k.n) changes by a large fraction over one
+                    // tile), the exact product of the high parts and one two_sum; the low parts,
+                    // the product's rounding error and the FP32 quadratic and cubic terms gathered
+                    // in the low word (an unnormalised pair, which the product below accepts)
+                    auto geom2 = [&](int f0, int f1) {
+                        const unsigned long long G1H = f2pack(ts.g1h[f0], ts.g1h[f1]);
+                        const unsigned long long Pp = fmul2(G1H, TT);
+                        const unsigned long long PE = ffma2(G1H, TT, fneg2(Pp));
+                        unsigned long long S, E;
+                        two_sum2(f2pack(ts.g0h[f0], ts.g0h[f1]), Pp, S, E);
+                        const unsigned long long Q =
+                            fmul2(TT2, ffma2(TT, f2pack(ts.g3[f0], ts.g3[f1]), f2pack(ts.g2[f0], ts.g2[f1])));
+                        const unsigned long long L =
+                            fadd2(E, fadd2(ffma2(f2pack(ts.g1l[f0], ts.g1l[f1]), TT, f2pack(ts.g0l[f0], ts.g0l[f1])),
+                                           fadd2(PE, Q)));
+                        return ff2{S, L};
+                    };
+                    const ff2 EP = {ld2(0), ld2(1)}, EC = {ld2(2), ld2(3)};
+                    const ff2 RP = {f2pack(rp[r].hi, rp[r].hi), f2pack(rp[r].lo, rp[r].lo)};
+                    const ff2 RC = {f2pack(rc[r].hi, rc[r].hi), f2pack(rc[r].lo, rc[r].lo)};
+                    const ff2 Y = ff_add2(ff_mul2(geom2(l0, l1), ff_sub2(EP, RP)),
+                                          ff_mul2(geom2(6 + l0, 6 + l1), ff_sub2(EC, RC)));
+                    f2unpack(Y.hi, y[l0].hi, y[l1].hi);
+                    f2unpack(Y.lo, y[l0].lo, y[l1].lo);
                 }
                 const int64_t k = ts.k_lo + j;
                 if (KIND == KIND_PROJECT) {
@@ -1369,7 +1439,7 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
             }
             __syncthreads();
             // ---- link difference tables
-            build_tables<false, RLY, 5>(smf, ybase(0), MX_AY, 6 * MX_AY, 6, ny);
+            build_tables2<false, RLY, 5>(smf, ybase(0), MX_AY, 6 * MX_AY, 3, ny);
             __syncthreads();
             // ---- X, Y, Z
             const int nbb = (nb + TB - 1) / TB;
