@@ -260,6 +260,10 @@ struct MxShared {
     // per delayed term: nested minus summed total delay at the reference output (fixed point,
     // constant over a tile; 0 for summed delays), the reference index offset and fraction
     TermRef tref[NTERM];
+    // per delayed term, for the items of even and odd index b: the shared-memory offsets of the
+    // third-difference entries x .. x + 7 of the term's fast-path window start x = 4 b + HL +
+    // tfm - h, less b / 2 (the link array's base and the 8-phase layout folded in)
+    int4 toff[NTERM][2][2];
     float redf[2 * (MIXED_THREADS / 32)];  // likelihood block sums
 };
 
@@ -765,6 +769,23 @@ __device__ void tdi_refs(const FwdParams &P, const TileSetup &ts, MxShared &sh, 
     const Split s = split_fx(((long long)nlr << FX_BITS) - D);
     sh.tref[id].tfm = s.m - nlr;
     sh.tref[id].tehi = s.ehi;
+    {
+        const int yb = ybase(c_tdimx.link[ch][c][q]) + A_E * MX_AY;
+        const int K = P.HL + (s.m - nlr) - (T - 2) / 2;
+        int o[16];
+#pragma unroll
+        for (int par = 0; par < 2; ++par)
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int v = 4 * par + K + r;  // floor division and modulo by shift and mask
+                o[8 * par + r] = yb + (v & 7) * RLY + (v >> 3);
+            }
+#pragma unroll
+        for (int par = 0; par < 2; ++par) {
+            sh.toff[id][par][0] = make_int4(o[8 * par], o[8 * par + 1], o[8 * par + 2], o[8 * par + 3]);
+            sh.toff[id][par][1] = make_int4(o[8 * par + 4], o[8 * par + 5], o[8 * par + 6], o[8 * par + 7]);
+        }
+    }
     constexpr int NUP = mx_nup(T);
     float2 *w = reinterpret_cast<float2 *>(tw) + id * NUP;
     if constexpr (T >= 4) {
@@ -1140,13 +1161,12 @@ __device__ __forceinline__ void tdi_chain(const FwdParams &P, const MxShared &sh
         bool fast = (m0 - nl0 == tr.tfm) && (m0 - h >= 0) && (m0 + kmax + h < ny);
 #pragma unroll
         for (int k = 1; k < TB; ++k) fast = fast && (k >= kmax || (eh + el[k] >= 0.0f && eh + el[k] < 1.0f));
-        const int yb = ybase(lk);
         const float q0 = eh * (eh - 1.0f), g = 2.0f * eh - 1.0f;
         if (fast) {
-            const int x = m0 - h;
-            int o[8];
-#pragma unroll
-            for (int r = 0; r < 8; ++r) o[r] = phy(x + r);
+            // offsets of the third differences e[x + r] (x = m0 - h), from the tile's table
+            const int hb = b >> 1;
+            const int4 ta = sh.toff[id][b & 1][0], tb = sh.toff[id][b & 1][1];
+            const int o[8] = {hb + ta.x, hb + ta.y, hb + ta.z, hb + ta.w, hb + tb.x, hb + tb.y, hb + tb.z, hb + tb.w};
             float C[TB];
 #pragma unroll
             for (int k = 0; k < TB; ++k) C[k] = 0.0f;
@@ -1157,7 +1177,7 @@ __device__ __forceinline__ void tdi_chain(const FwdParams &P, const MxShared &sh
                 unsigned long long win[RW];
 #pragma unroll
                 for (int a = 0; a < RW; ++a) {
-                    const float v = a < NE ? smf[yb + A_E * MX_AY + o[a & 7] + (a >> 3)] : 0.0f;
+                    const float v = a < NE ? smf[o[a & 7] + (a >> 3)] : 0.0f;
                     win[a] = f2pack(v, v);
                 }
                 unsigned long long acc[TB];  // (sum U e, sum dU e)
@@ -1176,7 +1196,7 @@ __device__ __forceinline__ void tdi_chain(const FwdParams &P, const MxShared &sh
 #pragma unroll
                     for (int e = a + RW; e < a + RW + 2; ++e)  // e[a], e[a+1] are no longer read
                         if (e < NE) {
-                            const float v = smf[yb + A_E * MX_AY + o[e & 7] + (e >> 3)];
+                            const float v = smf[o[e & 7] + (e >> 3)];
                             win[e % RW] = f2pack(v, v);
                         }
                 }
@@ -1193,7 +1213,9 @@ __device__ __forceinline__ void tdi_chain(const FwdParams &P, const MxShared &sh
             for (int pr = 0; pr < TB / 2; ++pr) {
                 const int k0 = 2 * pr, k1 = 2 * pr + 1;
                 const int a0 = o[(h + k0) & 7] + ((h + k0) >> 3), a1 = o[(h + k1) & 7] + ((h + k1) >> 3);
-                auto ld = [&](int arr) { return f2pack(smf[yb + arr * MX_AY + a0], smf[yb + arr * MX_AY + a1]); };
+                auto ld = [&](int arr) {
+                    return f2pack(smf[(arr - A_E) * MX_AY + a0], smf[(arr - A_E) * MX_AY + a1]);
+                };
                 acc_term2<T>(HI[pr], LO[pr], SM[pr], ld(A_SHI), ld(A_SLO), ld(A_DHI), ld(A_DLO), ld(A_A), EH, NEH,
                              f2pack(el[k0], el[k1]), G2, Q02, f2pack(-C[k0], -C[k1]));
             }
