@@ -477,6 +477,67 @@ __device__ __forceinline__ double f2d_pow2(float f, int k)
 __device__ __forceinline__ double ff2d_scaled(float hi, float lo, int se) { return f2d_scaled(hi, se) + f2d_scaled(lo, se); }
 
 
+// comp_weights_d (lr_mixed.cuh) with its two triple running sums taken on packed (w, dw/deps)
+// pairs: W[a] = (U_a, dU_a/deps), each lane the scalar sums, so the values are identical.
+template <int T>
+__device__ __forceinline__ void comp_weights_d2(float e, unsigned long long *W)
+{
+    constexpr int h = (T - 2) / 2;
+    float w[T], wd[T];
+    float L = 1.0f, Ld = 0.0f;
+#pragma unroll
+    for (int a = 0; a < T; ++a) {
+        w[a] = L;
+        wd[a] = Ld;
+        const float c1 = 1.0f / (float)(a + 1), c0 = (float)(h - a) / (float)(a + 1);
+        const float f = fmaf(e, c1, c0);
+        Ld = fmaf(Ld, f, L * c1);
+        L = L * f;
+    }
+    float R = 1.0f, Rd = 0.0f;
+#pragma unroll
+    for (int a = T - 1; a >= 0; --a) {
+        const float sg = ((T - 1 - a) & 1) ? -1.0f : 1.0f;
+        wd[a] = sg * fmaf(wd[a], R, w[a] * Rd);
+        w[a] = sg * w[a] * R;
+        const float c1 = 1.0f / (float)(T - a), c0 = (float)(h - a) / (float)(T - a);
+        const float g = fmaf(e, c1, c0);
+        Rd = fmaf(Rd, g, R * c1);
+        R = R * g;
+    }
+    w[h - 1] -= 0.5f * e * (e - 1.0f);
+    w[h] -= (1.0f - e) * (1.0f + e);
+    w[h + 1] -= 0.5f * e * (e + 1.0f);
+    wd[h - 1] -= e - 0.5f;
+    wd[h] += 2.0f * e;
+    wd[h + 1] -= e + 0.5f;
+    // triple running sums: from the left end left of the centre, from the right end from it on
+    unsigned long long s1 = 0ull, s2 = 0ull, s3 = 0ull;
+#pragma unroll
+    for (int a = 0; a < h; ++a) {
+        s1 = fadd2(s1, f2pack(w[a], wd[a]));
+        s2 = fadd2(s2, s1);
+        s3 = fadd2(s3, s2);
+        if (a <= T - 4) W[a] = s3;
+    }
+    unsigned long long t1 = 0ull, t2 = 0ull, t3 = 0ull, u1[T], u2[T];
+#pragma unroll
+    for (int a = T - 2; a >= h; --a) {
+        t1 = fsub2(t1, f2pack(w[a + 1], wd[a + 1]));
+        u1[a] = t1;
+    }
+#pragma unroll
+    for (int a = T - 3; a >= h; --a) {
+        t2 = fsub2(t2, u1[a + 1]);
+        u2[a] = t2;
+    }
+#pragma unroll
+    for (int a = T - 4; a >= h; --a) {
+        t3 = fsub2(t3, u2[a + 1]);
+        W[a] = t3;
+    }
+}
+
 // Difference tables of staged float-float series (arrays at base + k * AS, 8-phase index with
 // row length RL): d = s_{j+1} - s_j and a = (d_j - d_{j-1})/2 in float-float (ALO: the low part
 // of a kept in its own array, else folded into a), e = d_{j+2} - 2 d_{j+1} + d_j in FP32.
@@ -790,10 +851,14 @@ __device__ void tdi_refs(const FwdParams &P, const TileSetup &ts, MxShared &sh, 
     float2 *w = reinterpret_cast<float2 *>(tw) + id * NUP;
     if constexpr (T >= 4) {
         constexpr int NU = T - 3;
-        float U[NU], U1[NU];
-        comp_weights_d<T>(s.ehi, U, U1);
+        unsigned long long W[NU];
+        comp_weights_d2<T>(s.ehi, W);
 #pragma unroll
-        for (int a = 0; a < NUP; ++a) w[a] = a < NU ? make_float2(U[a], U1[a]) : make_float2(0.0f, 0.0f);
+        for (int a = 0; a < NUP; ++a) {
+            float u = 0.0f, u1 = 0.0f;
+            if (a < NU) f2unpack(W[a], u, u1);
+            w[a] = make_float2(u, u1);
+        }
     } else {
 #pragma unroll
         for (int a = 0; a < NUP; ++a) w[a] = make_float2(0.0f, 0.0f);
@@ -965,12 +1030,7 @@ __device__ __forceinline__ void proj_item(float *smf, const TileSetup &sh, int r
     const float eref = kmax == PB ? eh[PB / 2] : eh[0];
     // correction weights and their derivative as packed (U_a, dU_a/deps) pairs
     unsigned long long W[NU];
-    if constexpr (T >= 4) {
-        float U0[NU], U1[NU];
-        comp_weights_d<T>(eref, U0, U1);
-#pragma unroll
-        for (int a = 0; a < NU; ++a) W[a] = f2pack(U0[a], U1[a]);
-    }
+    if constexpr (T >= 4) comp_weights_d2<T>(eref, W);
 #pragma unroll 1
     for (int pol = 0; pol < 2; ++pol) {
         float C[PB];
@@ -1451,13 +1511,20 @@ __global__ void __launch_bounds__(MIXED_THREADS, (T <= 32 ? 2 : 1)) k_mixed(FwdP
             }
             // link delays of the outputs: at each item's first output (fixed point) and the
             // increments to the item's other outputs (rows padded to whole items)
-            const int nb4 = (nb + TB - 1) & ~(TB - 1);
-            for (int idx = tid; idx < 6 * nb4; idx += blockDim.x) {
-                const int l = idx / nb4, i = idx - l * nb4, i0 = i & ~(TB - 1);
-                const long long Li = piece_at(ts.dp[i < ts.jswt ? 0 : 1][l], i - ts.ic);
+            static_assert(TB == 4, "one float4 of increments per TDI item");
+            const int nbt = (nb + TB - 1) / TB;
+            for (int idx = tid; idx < 6 * nbt; idx += blockDim.x) {
+                const int l = idx / nbt, bi = idx - l * nbt, i0 = TB * bi;
                 const long long L0 = piece_at(ts.dp[i0 < ts.jswt ? 0 : 1][l], i0 - ts.ic);
-                dLf[l * LT + i] = (float)(Li - L0);
-                if (i == i0) Lblk[l * LB + i / TB] = Li;
+                Lblk[l * LB + bi] = L0;
+                float d[TB];
+                d[0] = 0.0f;
+#pragma unroll
+                for (int k = 1; k < TB; ++k) {
+                    const int i = i0 + k;
+                    d[k] = (float)(piece_at(ts.dp[i < ts.jswt ? 0 : 1][l], i - ts.ic) - L0);
+                }
+                reinterpret_cast<float4 *>(dLf + l * LT)[bi] = make_float4(d[0], d[1], d[2], d[3]);
             }
             __syncthreads();
             // ---- link difference tables
