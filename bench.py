@@ -40,9 +40,10 @@ FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (nominal; our DFMA probe measured 1.20
 # FP32 ALU peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per output sample of the fused mixed kernel at order 25 and its
-# default tile, from one ncu capture of a 16-source batch (236.5 MB / 7 115 014 outputs); the
-# launch traffic is this times the launch's outputs.  Valid only for that kernel build.
-MIXED_P25_DRAM_BYTES_PER_SAMPLE = 236_457_472 / 7_115_014
+# default tile (340), from one ncu capture of a 16-source batch (114.6 MB read + 121.4 MB written
+# / 7 115 014 outputs); the launch traffic is this times the launch's outputs.  Valid only for the
+# kernel build it was taken on (profiles/k_mixed_fused_batched16_p25.md).
+MIXED_P25_DRAM_BYTES_PER_SAMPLE = 235_981_568 / 7_115_014
 
 
 def workload(rank: int, world: int, n_sources: int):
