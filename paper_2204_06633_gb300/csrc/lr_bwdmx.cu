@@ -111,6 +111,18 @@ __device__ __forceinline__ void ff_fma_acc2(ff &acc, float whi, float wlo, float
     acc.lo += s.lo + fmaf(whi, glo, fmaf(wlo, ghi, pe));
 }
 
+// ff_fma_acc2 on both lanes of packed pairs (each lane the scalar operations)
+__device__ __forceinline__ void ff_fma_acc2x2(ff2 &acc, unsigned long long wh, unsigned long long wl,
+                                              unsigned long long gh, unsigned long long gl)
+{
+    const unsigned long long p = fmul2(wh, gh);
+    const unsigned long long pe = ffma2(wh, gh, fneg2(p));
+    unsigned long long s, e;
+    two_sum2(acc.hi, p, s, e);
+    acc.hi = s;
+    acc.lo = fadd2(acc.lo, fadd2(e, ffma2(wh, gl, ffma2(wl, gh, pe))));
+}
+
 __device__ __forceinline__ void block_max_u64(unsigned long long *dst, unsigned long long b)
 {
 #pragma unroll
@@ -129,7 +141,9 @@ __device__ __forceinline__ void block_max_u64(unsigned long long *dst, unsigned 
 // with W0 exact in float-float and the derivatives from the product w_a = Q_a N_a: N_a the (at most
 // two) factors eps / (a - h) and (eps - 1) / (a - h - 1) of the nodes next to the read, which can be
 // small, differentiated exactly; Q_a the other factors (|eps + h - i| >= 1), differentiated through
-// the sums S_k = sum 1 / (eps + h - i)^k (S1 in float-float).  The fourth-order term is below
+// the sums S_k = sum 1 / (eps + h - i)^k (S1 in float-float); the product and the sums are formed
+// once per term over all far nodes, and each tap divides its own factor out (O(T) per term instead
+// of O(T) per tap).  The fourth-order term is below
 // 1e-13 for |Delta| <= 5e-5.  Terms whose window crosses an integer sample (a different stencil) or
 // drifts further take exact float-float weights read by read.
 
@@ -140,26 +154,87 @@ __device__ __forceinline__ ff recip_signed(int d)
     return d < 0 ? ff_neg(r) : r;
 }
 
-// reference weight and Taylor coefficients of tap a at eps (float-float): out = W0.hi, W0.lo, W1,
-// W2, W3
+// 1/x in float-float (~2^-46) for |x| >= 1
+__device__ __forceinline__ ff recip_ff(ff x)
+{
+    const float r = 1.0f / x.hi;
+    const float er = fmaf(-x.hi, r, 1.0f) - x.lo * r;
+    return fast_two_sum(r, er * r);
+}
+
+// Constant factors of the reference weights.  With c_i = h - i (i < h) and i - h - 1 (i > h + 1),
+// every factor x_i / c_i = (eps + h - i) / c_i of the far nodes lies in [1, 2) in magnitude, and
+//   Q_a = prod_{i != a, h, h+1} x_i / (a - i) = P K_a / x_a   (outer taps),   P K_a   (a = h, h + 1)
+// with P = prod_{i != h, h+1} x_i / c_i (one product per term) and K_a = c_a prod_{i != a, h, h+1}
+// c_i / (a - i) (outer) or prod_{i != h, h+1} c_i / (a - i) (central), float-float constants.
 template <int T>
-__device__ void ref_weight_taylor(ff e, int a, float *out)
+struct KKTab {
+    float hi[T], lo[T];
+};
+template <int T>
+constexpr KKTab<T> make_kk_tab()
+{
+    KKTab<T> t{};
+    constexpr int h = (T - 2) / 2;
+    for (int a = 0; a < T; ++a) {
+        double K = 1.0;
+        for (int i = 0; i < T; ++i) {
+            if (i == a || i == h || i == h + 1) continue;
+            K *= (double)(i < h ? h - i : i - h - 1) / (double)(a - i);
+        }
+        if (a != h && a != h + 1) K *= (double)(a < h ? h - a : a - h - 1);
+        t.hi[a] = (float)K;
+        t.lo[a] = (float)(K - (double)(float)K);
+    }
+    return t;
+}
+template <int T>
+__constant__ KKTab<T> c_kk = make_kk_tab<T>();
+
+// per term, at its reference fraction eps: P and the sums S_k = sum_{i != h, h+1} 1 / x_i^k
+// (S1 in float-float, S2 and S3 in FP32)
+struct TermSums {
+    ff P, S1;
+    float S2, S3;
+};
+
+template <int T>
+__device__ TermSums term_sums(ff e)
 {
     constexpr int h = (T - 2) / 2;
-    ff Q = {1.0f, 0.0f}, S1 = {0.0f, 0.0f};
-    float S2 = 0.0f, S3 = 0.0f;
+    TermSums r = {{1.0f, 0.0f}, {0.0f, 0.0f}, 0.0f, 0.0f};
 #pragma unroll 1
     for (int i = 0; i < T; ++i) {
-        if (i == a || i == h || i == h + 1) continue;
+        if (i == h || i == h + 1) continue;
         const ff x = ff_add_f(e, (float)(h - i));  // exact: |x| >= 1
-        Q = ff_mul(Q, ff_mul(x, recip_signed(a - i)));
-        const float r = 1.0f / x.hi;
-        const float er = fmaf(-x.hi, r, 1.0f) - x.lo * r;
-        const ff rx = fast_two_sum(r, er * r);  // 1/x to ~2^-46
-        S1 = ff_add(S1, rx);
+        const int ci = i < h ? h - i : i - h - 1;
+        r.P = ff_mul(r.P, ff_mul(x, ff{c_recip.hi[ci], c_recip.lo[ci]}));
+        const ff rx = recip_ff(x);
+        r.S1 = ff_add(r.S1, rx);
         const float r2 = rx.hi * rx.hi;
-        S2 += r2;
-        S3 = fmaf(r2, rx.hi, S3);
+        r.S2 += r2;
+        r.S3 = fmaf(r2, rx.hi, r.S3);
+    }
+    return r;
+}
+
+// reference weight and Taylor coefficients of tap a at eps (float-float), from the term's sums:
+// the tap's own factor divided out of P and subtracted from the sums; out = W0.hi, W0.lo, W1,
+// W2, W3
+template <int T>
+__device__ void ref_weight_taylor(ff e, int a, const TermSums &ts, float *out)
+{
+    constexpr int h = (T - 2) / 2;
+    const ff K = {c_kk<T>.hi[a], c_kk<T>.lo[a]};
+    ff Q = ff_mul(ts.P, K), S1 = ts.S1;
+    float S2 = ts.S2, S3 = ts.S3;
+    if (a != h && a != h + 1) {
+        const ff rx = recip_ff(ff_add_f(e, (float)(h - a)));
+        Q = ff_mul(Q, rx);
+        S1 = ff_sub(S1, rx);
+        const float r2 = rx.hi * rx.hi;
+        S2 -= r2;
+        S3 -= r2 * rx.hi;
     }
     ff N, N1;
     float N2 = 0.0f;
@@ -200,27 +275,29 @@ __device__ __forceinline__ ff weight_ff(ff e, int a)
 
 constexpr float TAYLOR_MAX_DELTA = 5e-5f;
 
-// Shared memory: Lf[6][WN] (int64, link delays in fixed point samples), Dq[WN] (int64, running
-// chained delay of the current chain), Ghi, Glo [3][WN] (float), Mo[WN] (int), Dl[WN] (float, the
-// offset of each output's fraction from the term's reference), Rf[42][5][T] (float: W0 hi, W0 lo,
-// W1, W2, W3 of every term and tap).
+// Shared memory, every float array stored as (value at i, value at i + 1) pairs so that two
+// consecutive taps of the gather come on the two lanes of one packed f32x2 load: RP[42][5][T]
+// (W0 hi, W0 lo, W1, W2, W3 of every term and tap, as (W[a], W[a - 1])), Lf[6][WN] (int64, link
+// delays in fixed point samples), Dq[WN] (int64, running chained delay of the current chain),
+// Gx, Gy [3][WN] (high and low words of the scaled cotangent, as (g[j], g[j + 1])), D2[WN] (the
+// offset of each output's fraction from the term's reference, as (d[j], d[j + 1])), Mo[WN] (int).
 template <int T>
 __global__ void __launch_bounds__(256, 2) k_tdi_adj_mx(FwdParams P, BwdParams B)
 {
     constexpr int h = (T - 2) / 2;
     extern __shared__ __align__(16) long long smi[];
     const int WN = B.wn;
-    long long *Lf = smi, *Dq = smi + 6 * WN;
-    float *Ghi = reinterpret_cast<float *>(smi + 7 * WN), *Glo = Ghi + 3 * WN;
-    int *Mo = reinterpret_cast<int *>(Glo + 3 * WN);
-    float *Dl = reinterpret_cast<float *>(Mo + WN);
-    float *Rf = Dl + WN;
+    float2 *RP = reinterpret_cast<float2 *>(smi);
+    long long *Lf = reinterpret_cast<long long *>(RP + NTERM_BW * 5 * T), *Dq = Lf + 6 * WN;
+    float2 *Gx = reinterpret_cast<float2 *>(Dq + WN), *Gy = Gx + 3 * WN, *D2 = Gy + 3 * WN;
+    int *Mo = reinterpret_cast<int *>(D2 + WN);
     __shared__ TileInfo ti;
     __shared__ int mo_lo, mo_hi;
     __shared__ unsigned dmax_bits;
     __shared__ unsigned long long gmax;
     __shared__ long long dnest[NTERM_BW];
     __shared__ long long xref[NTERM_BW];  // each term's read offset at the window centre (fixed point)
+    __shared__ TermSums tsum[NTERM_BW];   // each term's product and reciprocal sums at its reference
     const int64_t total = P.total_tiles >= 0 ? P.total_tiles : P.src.tile_off[P.src.S];
     for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
         if (threadIdx.x == 0) {
@@ -267,6 +344,8 @@ __global__ void __launch_bounds__(256, 2) k_tdi_adj_mx(FwdParams P, BwdParams B)
             long long D = 0;
             for (int qq = 1; qq <= q; ++qq) D += Lf[c_tdibm.pair[ch][c][qq] * WN + jref];
             xref[id] = -(D + dnest[id]);
+            const Split sr = split_fx(xref[id]);
+            tsum[id] = term_sums<T>(ff{sr.ehi, sr.elo});
         }
         const int se = scale_exp(gmax);
         const double up = exp2((double)se), down = exp2((double)-se);
@@ -275,8 +354,13 @@ __global__ void __launch_bounds__(256, 2) k_tdi_adj_mx(FwdParams P, BwdParams B)
             const bool in = n >= 0 && n < N;
             for (int c = 0; c < 3; ++c) {
                 const ff v = in ? ff_scaled(__ldg(gx + c * N + n), up) : ff{0.0f, 0.0f};
-                Ghi[c * WN + j] = v.hi;
-                Glo[c * WN + j] = v.lo;
+                Gx[c * WN + j].x = v.hi;
+                Gy[c * WN + j].x = v.lo;
+                if (j > 0) {
+                    Gx[c * WN + j - 1].y = v.hi;
+                    Gy[c * WN + j - 1].y = v.lo;
+                }
+                if (j == wn - 1) Gx[c * WN + j].y = Gy[c * WN + j].y = 0.0f;
             }
         }
         __syncthreads();
@@ -286,9 +370,14 @@ __global__ void __launch_bounds__(256, 2) k_tdi_adj_mx(FwdParams P, BwdParams B)
             if (id % 7 + 1 > P.q_terms) continue;
             const Split s = split_fx(xref[id]);
             float out[5];
-            ref_weight_taylor<T>(ff{s.ehi, s.elo}, a, out);
+            ref_weight_taylor<T>(ff{s.ehi, s.elo}, a, tsum[id], out);
 #pragma unroll
-            for (int f = 0; f < 5; ++f) Rf[(id * 5 + f) * T + a] = out[f];
+            for (int f = 0; f < 5; ++f) {
+                float2 *row = RP + (id * 5 + f) * T;
+                row[a].x = out[f];
+                if (a + 1 < T) row[a + 1].y = out[f];
+                if (a == 0) row[0].y = 0.0f;
+            }
         }
         ff acc[6];
 #pragma unroll
@@ -299,7 +388,7 @@ __global__ void __launch_bounds__(256, 2) k_tdi_adj_mx(FwdParams P, BwdParams B)
         if (me < nb) {
             const int jk = (int)(k - n_lo);
             for (int ch = 0; ch < 3; ++ch) {
-                const ff gv = {Ghi[ch * WN + jk], Glo[ch * WN + jk]};
+                const ff gv = {Gx[ch * WN + jk].x, Gy[ch * WN + jk].x};
 #pragma unroll
                 for (int l = 0; l < 6; ++l) {
                     if (l == c_tdibm.link[ch][0][0]) acc[l] = ff_add(acc[l], gv);
@@ -331,7 +420,9 @@ __global__ void __launch_bounds__(256, 2) k_tdi_adj_mx(FwdParams P, BwdParams B)
                         lmin = min(lmin, m);
                         lmax = max(lmax, m);
                         const float d = (float)(X - xr) * 0x1p-44f;  // exact difference, then rounded
-                        Dl[j] = d;
+                        D2[j].x = d;
+                        if (j > 0) D2[j - 1].y = d;
+                        if (j == wn - 1) D2[j].y = 0.0f;
                         dm = fmaxf(dm, fabsf(d));
                     }
                     atomicMin(&mo_lo, lmin);
@@ -347,13 +438,32 @@ __global__ void __launch_bounds__(256, 2) k_tdi_adj_mx(FwdParams P, BwdParams B)
                         const bool taylor = mo_lo == mo_hi && mo_lo == (int)(xr >> FX_BITS) &&
                                             __uint_as_float(dmax_bits) <= TAYLOR_MAX_DELTA;
                         if (taylor) {
-                            const float *R0h = Rf + (id * 5) * T, *R0l = R0h + T, *R1 = R0l + T, *R2 = R1 + T,
-                                        *R3 = R2 + T;
-                            for (int j = jlo; j <= jhi; ++j) {
-                                const int a = (int)(k - (n_lo + j + mo_lo)) + h;  // in [0, T): one stencil
-                                const float d = Dl[j];
-                                const float corr = d * fmaf(d, fmaf(d, R3[a], R2[a]), R1[a]);
-                                ff_fma_acc2(s, R0h[a], R0l[a] + corr, Ghi[ch * WN + j], Glo[ch * WN + j]);
+                            // taps j and j + 1 (coefficient rows at a and a - 1) on the two lanes of
+                            // packed pairs, two interleaved partial sums; an odd last tap alone
+                            const unsigned long long *Rt =
+                                reinterpret_cast<const unsigned long long *>(RP + id * 5 * T);
+                            const unsigned long long *Gxc = reinterpret_cast<const unsigned long long *>(Gx + ch * WN);
+                            const unsigned long long *Gyc = reinterpret_cast<const unsigned long long *>(Gy + ch * WN);
+                            const unsigned long long *Dc = reinterpret_cast<const unsigned long long *>(D2);
+                            int a = (int)(k - (n_lo + jlo + mo_lo)) + h;  // in [0, T): one stencil
+                            ff2 S = {0ull, 0ull};
+                            int j = jlo;
+                            for (; j < jhi; j += 2, a -= 2) {
+                                const unsigned long long d = Dc[j];
+                                const unsigned long long corr =
+                                    fmul2(d, ffma2(d, ffma2(d, Rt[4 * T + a], Rt[3 * T + a]), Rt[2 * T + a]));
+                                ff_fma_acc2x2(S, Rt[a], fadd2(Rt[T + a], corr), Gxc[j], Gyc[j]);
+                            }
+                            float h0, h1, l0, l1;
+                            f2unpack(S.hi, h0, h1);
+                            f2unpack(S.lo, l0, l1);
+                            s = ff_add(ff{h0, l0}, ff{h1, l1});
+                            if (j == jhi) {
+                                const float *Rs = reinterpret_cast<const float *>(RP + id * 5 * T);
+                                const float d = D2[j].x;
+                                const float corr = d * fmaf(d, fmaf(d, Rs[2 * (4 * T + a)], Rs[2 * (3 * T + a)]),
+                                                            Rs[2 * (2 * T + a)]);
+                                ff_fma_acc2(s, Rs[2 * a], Rs[2 * (T + a)] + corr, Gx[ch * WN + j].x, Gy[ch * WN + j].x);
                             }
                         } else {
                             for (int j = jlo; j <= jhi; ++j) {
@@ -362,7 +472,7 @@ __global__ void __launch_bounds__(256, 2) k_tdi_adj_mx(FwdParams P, BwdParams B)
                                     const long long X = -(Dq[j] + dnest[id]);
                                     const Split sp = split_fx(X);
                                     const ff w = weight_ff<T>(ff{sp.ehi, sp.elo}, a);
-                                    ff_fma_acc2(s, w.hi, w.lo, Ghi[ch * WN + j], Glo[ch * WN + j]);
+                                    ff_fma_acc2(s, w.hi, w.lo, Gx[ch * WN + j].x, Gy[ch * WN + j].x);
                                 }
                             }
                         }
@@ -817,7 +927,7 @@ size_t smem_bwd_mx(int kind, int order, const FwdParams &P, const BwdParams &B)
 {
     const size_t T = (size_t)order + 1;
     if (kind == 2) return sizeof(float) * 4 * (size_t)P.wmax;
-    return kind == 0 ? (size_t)B.wn * (7 * 8 + 6 * 4 + 4 + 4) + (size_t)NTERM_BW * 5 * T * 4
+    return kind == 0 ? (size_t)B.wn * (7 * 8 + 6 * 8 + 8 + 4) + (size_t)NTERM_BW * 5 * T * 8
                      : (size_t)B.wk * (27 * 8 + 2 * T * 4 + 4);
 }
 

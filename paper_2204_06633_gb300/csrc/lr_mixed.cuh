@@ -214,4 +214,99 @@ __device__ __forceinline__ void comp_weights_d(float e, float *U, float *U1)
     triple_sums<T>(wd, U1);
 }
 
+// ---------------------------------------------------------------- packed f32x2 pairs
+// packed pairs of FP32 values and their fused multiply-add (fma.rn.f32x2: two IEEE FMAs in one
+// instruction)
+__device__ __forceinline__ unsigned long long f2pack(float a, float b)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+__device__ __forceinline__ void f2unpack(unsigned long long r, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ unsigned long long fsub2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ unsigned long long fmul2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// both lanes negated (sign bits flipped)
+__device__ __forceinline__ unsigned long long fneg2(unsigned long long a) { return a ^ 0x8000000080000000ull; }
+
+// two_sum on both lanes of packed pairs (each lane exactly the scalar two_sum)
+__device__ __forceinline__ void two_sum2(unsigned long long a, unsigned long long b, unsigned long long &s,
+                                         unsigned long long &e)
+{
+    s = fadd2(a, b);
+    const unsigned long long bb = fsub2(s, a);
+    e = fadd2(fsub2(a, fsub2(s, bb)), fsub2(b, bb));
+}
+enum { A_SHI = 0, A_SLO, A_DHI, A_DLO, A_A, A_E, A_ALO };
+
+// 8-byte asynchronous global -> shared copy (completion: cp_async_wait_all by the issuing thread)
+// float-float arithmetic on both lanes of packed pairs: each lane performs exactly the IEEE
+// operations of the scalar ff_add / ff_sub / ff_mul (lr_mixed.cuh), so results are identical
+struct ff2 {
+    unsigned long long hi, lo;
+};
+
+__device__ __forceinline__ ff2 fast_two_sum2(unsigned long long a, unsigned long long b)
+{
+    const unsigned long long s = fadd2(a, b);
+    return {s, fsub2(b, fsub2(s, a))};
+}
+
+__device__ __forceinline__ ff2 ff_add2(ff2 a, ff2 b)
+{
+    unsigned long long s, e;
+    two_sum2(a.hi, b.hi, s, e);
+    return fast_two_sum2(s, fadd2(e, fadd2(a.lo, b.lo)));
+}
+
+// a - b as a + (-b): the negation is exact, so each operation below rounds as its scalar
+// counterpart with the negated operand
+__device__ __forceinline__ ff2 ff_sub2(ff2 a, ff2 b)
+{
+    const unsigned long long s = fsub2(a.hi, b.hi);
+    const unsigned long long bb = fsub2(s, a.hi);
+    const unsigned long long e = fsub2(fsub2(a.hi, fsub2(s, bb)), fadd2(b.hi, bb));
+    return fast_two_sum2(s, fadd2(e, fsub2(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ ff2 ff_mul2(ff2 a, ff2 b)
+{
+    const unsigned long long p = fmul2(a.hi, b.hi);
+    unsigned long long e = ffma2(a.hi, b.hi, fneg2(p));
+    e = ffma2(a.hi, b.lo, e);
+    e = ffma2(a.lo, b.hi, e);
+    return fast_two_sum2(p, e);
+}
+
 }  // namespace lr
