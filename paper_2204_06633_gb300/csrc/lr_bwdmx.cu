@@ -686,7 +686,9 @@ __global__ void __launch_bounds__(256, 2) k_proj_adj_mx(FwdParams P, BwdParams B
 // link response (patterns, 1/(2(1 - k.n)) and the read times through k), as the FP64 kernel, with
 // the strain reads and their derivative reads in float-float: value and derivative weights from
 // float-float prefix and suffix products (product rule), float-float strain (scaled per tile by a
-// power of two).  The geometry and the assembly against g_y stay FP64.
+// power of two).  The geometry and the assembly against g_y stay FP64; a link and its reverse
+// share the arm's unit vector (negated exactly), and the reads' power-of-two scale is undone once
+// on the tile's sums.
 
 struct LinkGeoN {
     double xp, xc, kn, den;
@@ -788,7 +790,7 @@ __device__ __forceinline__ void read_vd_mx(const float *sm, int wstride, int64_t
 }
 
 template <int T>
-__global__ void __launch_bounds__(256) k_sky_adj_mx(FwdParams P, BwdParams B)
+__global__ void __launch_bounds__(256, 2) k_sky_adj_mx(FwdParams P, BwdParams B)
 {
     constexpr int h = (T - 2) / 2;
     extern __shared__ __align__(16) float sms[];  // h+ hi, h+ lo, hx hi, hx lo: [4][wmax]
@@ -853,40 +855,58 @@ __global__ void __launch_bounds__(256) k_sky_adj_mx(FwdParams P, BwdParams B)
                 for (int i = 0; i < 3; ++i)
                     sig[i] = (skc.k[0] * x[3 * i] + skc.k[1] * x[3 * i + 1] + skc.k[2] * x[3 * i + 2]) / C_LIGHT *
                              P.inv_dt;
+                // reads still scaled by the tile's power of two: every term below is linear in them,
+                // so the sums are unscaled once at the end of the tile
                 double Rp[3], Rpd[3], Rc[3], Rcd[3];
                 for (int r = 0; r < 3; ++r)
-                    read_vd_mx<T>(sms, WS, k, u0 - sig[r], w_lo, wlen, down, P.err, Rp[r], Rpd[r], Rc[r], Rcd[r]);
-                for (int l = 0; l < 6; ++l) {
-                    const double gl = __ldg(gy + l * ti.N + k);
-                    if (gl == 0.0) continue;
-                    const int LR[6] = {0, 1, 2, 0, 2, 1}, LS[6] = {1, 2, 0, 2, 1, 0};
-                    const int r = LR[l], s = LS[l];
+                    read_vd_mx<T>(sms, WS, k, u0 - sig[r], w_lo, wlen, 1.0, P.err, Rp[r], Rpd[r], Rc[r], Rcd[r]);
+                // arm a carries link a (receiver a, emitter a + 1) and its reverse 5 - a: the reverse
+                // has the unit vector negated exactly, so the patterns and their angle derivatives are
+                // the same and k.n and its derivatives change sign
+                for (int arm = 0; arm < 3; ++arm) {
+                    const double g0 = __ldg(gy + arm * ti.N + k), g1 = __ldg(gy + (5 - arm) * ti.N + k);
+                    if (g0 == 0.0 && g1 == 0.0) continue;
                     double nv[3];
-                    const LinkGeoN q = link_geo_n(skc, x, l, nv);
-                    double ep, epd, ec, ecd;
-                    read_vd_mx<T>(sms, WS, k, u0 - L[l] * P.inv_dt - sig[s], w_lo, wlen, down, P.err, ep, epd, ec, ecd);
-                    const double dPp = ep - Rp[r], dPc = ec - Rc[r];
-                    const double dH = q.xp * dPp + q.xc * dPc;
+                    const LinkGeoN q = link_geo_n(skc, x, arm, nv);
                     const double un = skc.u[0] * nv[0] + skc.u[1] * nv[1] + skc.u[2] * nv[2];
                     const double vn = skc.v[0] * nv[0] + skc.v[1] * nv[1] + skc.v[2] * nv[2];
+                    double dxp[2], dxc[2], dkn[2];
                     for (int th = 0; th < 2; ++th) {
                         const double da = du[th][0] * nv[0] + du[th][1] * nv[1] + du[th][2] * nv[2];
                         const double db = dv[th][0] * nv[0] + dv[th][1] * nv[1] + dv[th][2] * nv[2];
                         const double dxip = 2.0 * (un * da - vn * db), dxic = 2.0 * (da * vn + un * db);
-                        const double dxp = skc.c2p * dxip + skc.s2p * dxic, dxc = -skc.s2p * dxip + skc.c2p * dxic;
-                        const double dkn = dk[th][0] * nv[0] + dk[th][1] * nv[1] + dk[th][2] * nv[2];
-                        const double dden = 2.0 * q.den * q.den * dkn;
-                        const double due = -(dk[th][0] * x[3 * s] + dk[th][1] * x[3 * s + 1] + dk[th][2] * x[3 * s + 2]) /
-                                           C_LIGHT * P.inv_dt;
-                        const double dur = -(dk[th][0] * x[3 * r] + dk[th][1] * x[3 * r + 1] + dk[th][2] * x[3 * r + 2]) /
-                                           C_LIGHT * P.inv_dt;
-                        const double ddH = dxp * dPp + dxc * dPc + q.xp * (epd * due - Rpd[r] * dur) +
-                                           q.xc * (ecd * due - Rcd[r] * dur);
-                        G[th] = fma(gl, dden * dH + q.den * ddH, G[th]);
+                        dxp[th] = skc.c2p * dxip + skc.s2p * dxic;
+                        dxc[th] = -skc.s2p * dxip + skc.c2p * dxic;
+                        dkn[th] = dk[th][0] * nv[0] + dk[th][1] * nv[1] + dk[th][2] * nv[2];
                     }
-                    G[2] = fma(gl, q.den * (2.0 * q.xc * dPp - 2.0 * q.xp * dPc), G[2]);
+                    for (int rev = 0; rev < 2; ++rev) {
+                        const double gl = rev ? g1 : g0;
+                        if (gl == 0.0) continue;
+                        const int l = rev ? 5 - arm : arm;
+                        const int LR[6] = {0, 1, 2, 0, 2, 1}, LS[6] = {1, 2, 0, 2, 1, 0};
+                        const int r = LR[l], s = LS[l];
+                        const double sg = rev ? -1.0 : 1.0;
+                        const double den = rev ? 1.0 / (2.0 * (1.0 + q.kn)) : q.den;
+                        double ep, epd, ec, ecd;
+                        read_vd_mx<T>(sms, WS, k, u0 - L[l] * P.inv_dt - sig[s], w_lo, wlen, 1.0, P.err, ep, epd, ec,
+                                      ecd);
+                        const double dPp = ep - Rp[r], dPc = ec - Rc[r];
+                        const double dH = q.xp * dPp + q.xc * dPc;
+                        for (int th = 0; th < 2; ++th) {
+                            const double dden = 2.0 * den * den * (sg * dkn[th]);
+                            const double due = -(dk[th][0] * x[3 * s] + dk[th][1] * x[3 * s + 1] + dk[th][2] * x[3 * s + 2]) /
+                                               C_LIGHT * P.inv_dt;
+                            const double dur = -(dk[th][0] * x[3 * r] + dk[th][1] * x[3 * r + 1] + dk[th][2] * x[3 * r + 2]) /
+                                               C_LIGHT * P.inv_dt;
+                            const double ddH = dxp[th] * dPp + dxc[th] * dPc + q.xp * (epd * due - Rpd[r] * dur) +
+                                               q.xc * (ecd * due - Rcd[r] * dur);
+                            G[th] = fma(gl, dden * dH + den * ddH, G[th]);
+                        }
+                        G[2] = fma(gl, den * (2.0 * q.xc * dPp - 2.0 * q.xp * dPc), G[2]);
+                    }
                 }
             }
+            for (int t = 0; t < 3; ++t) G[t] *= down;
         }
         // fixed-order block reduction: warp tree, then warps in order
         for (int t = 0; t < 3; ++t) {
