@@ -739,8 +739,10 @@ __device__ void read_vd_ff(const float *phi, const float *plo, const float *chi,
         D = ff_add(ff_mul(D, f), ff_mul(L, r));
         L = ff_mul(L, f);
     }
-    vp = dp = vc = dc = ff{0.0f, 0.0f};
     const ff cp = {phi[st + h], plo[st + h]}, cc = {chi[st + h], clo[st + h]};
+    // h+ and hx on the two lanes of packed pairs (each lane the scalar float-float operations)
+    const ff2 C2 = {f2pack(cp.hi, cc.hi), f2pack(cp.lo, cc.lo)};
+    ff2 V = {0ull, 0ull}, DV = {0ull, 0ull};
     ff R = {1.0f, 0.0f}, RD = {0.0f, 0.0f};
 #pragma unroll 1
     for (int a = T - 1; a >= 0; --a) {
@@ -749,16 +751,18 @@ __device__ void read_vd_ff(const float *phi, const float *plo, const float *chi,
             w = ff_neg(w);
             dw = ff_neg(dw);
         }
-        const ff sp = ff_sub(ff{phi[st + a], plo[st + a]}, cp), sc = ff_sub(ff{chi[st + a], clo[st + a]}, cc);
-        ff_fma_acc2(vp, w.hi, w.lo, sp.hi, sp.lo);
-        ff_fma_acc2(dp, dw.hi, dw.lo, sp.hi, sp.lo);
-        ff_fma_acc2(vc, w.hi, w.lo, sc.hi, sc.lo);
-        ff_fma_acc2(dc, dw.hi, dw.lo, sc.hi, sc.lo);
+        const ff2 S = ff_sub2(ff2{f2pack(phi[st + a], chi[st + a]), f2pack(plo[st + a], clo[st + a])}, C2);
+        ff_fma_acc2x2(V, f2pack(w.hi, w.hi), f2pack(w.lo, w.lo), S.hi, S.lo);
+        ff_fma_acc2x2(DV, f2pack(dw.hi, dw.hi), f2pack(dw.lo, dw.lo), S.hi, S.lo);
         const ff r = {c_recip.hi[T - a], c_recip.lo[T - a]};
         const ff g = ff_mul(ff_add_f(e, (float)(h - a)), r);
         RD = ff_add(ff_mul(RD, g), ff_mul(R, r));
         R = ff_mul(R, g);
     }
+    f2unpack(V.hi, vp.hi, vc.hi);
+    f2unpack(V.lo, vp.lo, vc.lo);
+    f2unpack(DV.hi, dp.hi, dc.hi);
+    f2unpack(DV.lo, dp.lo, dc.lo);
     vp = ff_add(vp, cp);
     vc = ff_add(vc, cc);
 }
