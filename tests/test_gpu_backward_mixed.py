@@ -1,6 +1,7 @@
 """The mixed-precision adjoint (plans of precision LR_MIXED): TDI and projection transposes with
-float-float weights and float-float accumulation on the FP32 pipe, FP64 positions and delays, the
-sky gradient in FP64 on that g_y.  Against the FP64 oracle with white cotangents (residuals against noisy data, the
+float-float weights and float-float accumulation on the FP32 pipe, FP64 positions and delays; the
+sky gradient from float-float strain reads and derivative reads with FP64 geometry and assembly on
+that g_y.  Against the FP64 oracle with white cotangents (residuals against noisy data, the
 likelihood's use): strain gradients within 1e-6 relative L2; sky-angle gradients within 1e-6 or the
 rounding scale of the gradient sum at FP32 precision, 4 (T + 16) u32 sum|terms| (the sum's terms
 are up to ~1e8 times its value at low frequency); the adjoint identity against the mixed forward;
@@ -46,6 +47,26 @@ def test_mixed_backward_against_oracle(ctx, flex, p, N, f):
     t0h, hp, hc = synth.gb_input(src, T0, DT, N, p)
     plan = lr.Plan(ctx, p, N, DT, flex.gpu, t0=T0, precision=lr.MIXED)
     g = np.random.default_rng(4).normal(size=(3, N))
+    ghp, ghc, gsky = plan.backward(dev(hp), dev(hc), t0h, sky(src), dev(g))
+    plan.check()
+    rp, rc, rs, scale = oracle.backward(p, 2, DT, T0, N, flex.orc, flex.orc, hp, hc, t0h, src.lam, src.beta,
+                                        src.psi, g, with_scale=True)
+    eh = np.linalg.norm(np.r_[host(ghp) - rp, host(ghc) - rc]) / np.linalg.norm(np.r_[rp, rc])
+    assert eh <= 1e-6, eh
+    assert_sky_mixed(host(gsky), rs, scale, p + 1)
+
+
+@pytest.mark.parametrize("p", [1, 3, 5, 7, 9, 13, 15, 17, 19, 21, 23, 31])
+def test_mixed_backward_every_order(ctx, flex, p):
+    """Every other compiled order of the mixed adjoint against the oracle: the TDI transpose's
+    reference weights use per-order constant tables (order 1 has no far nodes at all, order 3
+    two), and the gathers' tap windows change with the order."""
+    import dataclasses
+    N = 2500
+    src = dataclasses.replace(synth.draw_sources(1, seed=6, A=1e-21)[0], f=3e-3)
+    t0h, hp, hc = synth.gb_input(src, T0, DT, N, p)
+    plan = lr.Plan(ctx, p, N, DT, flex.gpu, t0=T0, precision=lr.MIXED)
+    g = np.random.default_rng(7).normal(size=(3, N))
     ghp, ghc, gsky = plan.backward(dev(hp), dev(hc), t0h, sky(src), dev(g))
     plan.check()
     rp, rc, rs, scale = oracle.backward(p, 2, DT, T0, N, flex.orc, flex.orc, hp, hc, t0h, src.lam, src.beta,
