@@ -48,7 +48,7 @@ def test_frequency_band_flexing(ctx, orbits, f):
     assert e < RELMX
 
 
-@pytest.mark.parametrize("p", [1, 3, 5, 7, 11, 41])
+@pytest.mark.parametrize("p", [1, 3, 5, 7, 9, 11, 13, 15, 17, 19, 21, 23, 31, 41])
 def test_orders(ctx, orbits, p):
     src = synth.Source(A=1e-21, f=2e-3, fdot=1e-17, phi0=0.3, iota=0.7, psi=0.4, lam=1.0, beta=0.3)
     mixed(ctx, src, 12345, p, orbits["flex"])
